@@ -1,0 +1,313 @@
+/*
+ * FP64 CPU oracle for the two-stage adaptive AD-census stereo matcher of
+ * "Mixed Reality Depth Contour Occlusion Using Binocular Similarity Matching
+ * and Three-dimensional Contour Optimisation" (arXiv 2203.02300), Sect. 4.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header, table or constant with the CUDA
+ * library.
+ *
+ * Plain and slow on purpose: every aggregated cost is an explicit double
+ * sum over the support region, every cost term calls libm exp() in double.
+ * No prefix sums, no lookup tables, no blocking.  OpenMP (if enabled) only
+ * splits independent rows; each value is summed in the same order either way.
+ *
+ * Readings of points the paper leaves open (fixed here and in the tests):
+ *   - grey level  Y = (77 R + 150 G + 29 B + 128) >> 8  (integer)
+ *   - census (Sect. 4.2.1): cw x ch window (9x7) on Y, centre excluded,
+ *     clamp-to-edge, bit k = [Y(n) < Y(p)] with k running over window rows
+ *     top to bottom, columns left to right.
+ *   - C_AD = mean of the three absolute channel differences (grey levels),
+ *     C_census = Hamming distance of the census strings.
+ *   - arms (Sect. 4.1, colour + distance double threshold): arm length in
+ *     direction e is the largest k <= L1 such that for every 1 <= j <= k,
+ *     p + j e lies in the image, Dc(p_j, p) < tau1, Dc(p_j, p_{j-1}) < tau1,
+ *     and Dc(p_j, p) < tau2 whenever j > L2; Dc = max channel difference.
+ *   - L_min = the shortest of the four arms of p (Eq. 1).
+ *   - support region (Eq. 2): union over q on the vertical arm of p of q's
+ *     horizontal segment; N = its pixel count.  Reference-view arms only.
+ *   - d in [0, D-1]; a match outside the image costs 1 (upper bound of Eq. 1).
+ *   - WTA (Eq. 3) takes the smallest d among equal minima.
+ *   - outlier removal: left-right consistency, valid iff x - dL >= 0 and
+ *     |dL(x) - dR(x - dL)| <= tol, otherwise -1.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+/* ---------------------------------------------------------------- grey */
+static int grey_of(const uint8_t *px)
+{
+    return (77 * (int)px[0] + 150 * (int)px[1] + 29 * (int)px[2] + 128) >> 8;
+}
+
+int orc_grey(const uint8_t *rgb, int W, int H, int32_t *out)
+{
+    if (!rgb || !out || W < 1 || H < 1) return ORC_EINVAL;
+    for (long i = 0; i < (long)W * H; i++) out[i] = grey_of(rgb + 3 * i);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------------- census */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int orc_census(const uint8_t *rgb, int W, int H, int cw, int ch, uint64_t *out)
+{
+    if (!rgb || !out || W < 1 || H < 1) return ORC_EINVAL;
+    if (cw < 1 || ch < 1 || !(cw & 1) || !(ch & 1) || cw * ch - 1 > 64) return ORC_EINVAL;
+    int32_t *Y = (int32_t *)malloc(sizeof(int32_t) * (size_t)W * H);
+    if (!Y) return ORC_ENOMEM;
+    orc_grey(rgb, W, H, Y);
+    int rx = cw / 2, ry = ch / 2;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int yc = Y[(long)y * W + x];
+            uint64_t bits = 0;
+            int k = 0;
+            for (int dy = -ry; dy <= ry; dy++) {
+                for (int dx = -rx; dx <= rx; dx++) {
+                    if (dx == 0 && dy == 0) continue;
+                    int nx = clampi(x + dx, 0, W - 1), ny = clampi(y + dy, 0, H - 1);
+                    if (Y[(long)ny * W + nx] < yc) bits |= (uint64_t)1 << k;
+                    k++;
+                }
+            }
+            out[(long)y * W + x] = bits;
+        }
+    }
+    free(Y);
+    return ORC_OK;
+}
+
+int orc_hamming(uint64_t a, uint64_t b)
+{
+    uint64_t v = a ^ b;
+    int n = 0;
+    while (v) { n += (int)(v & 1u); v >>= 1; }
+    return n;
+}
+
+/* ---------------------------------------------------------------- arms */
+static int dc_max(const uint8_t *a, const uint8_t *b)
+{
+    int m = 0;
+    for (int c = 0; c < 3; c++) {
+        int v = abs((int)a[c] - (int)b[c]);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
+/* arms: 4 bytes per pixel, order {left, right, up, down} */
+int orc_arms(const uint8_t *rgb, int W, int H, int L1, int L2, int tau1, int tau2,
+             uint8_t *arms)
+{
+    if (!rgb || !arms || W < 1 || H < 1 || L1 < 0 || L1 > 255 || L2 < 0) return ORC_EINVAL;
+    static const int ex[4] = {-1, 1, 0, 0}, ey[4] = {0, 0, -1, 1};
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            const uint8_t *p = rgb + 3 * ((long)y * W + x);
+            for (int e = 0; e < 4; e++) {
+                int k = 0;
+                for (int j = 1; j <= L1; j++) {
+                    int qx = x + j * ex[e], qy = y + j * ey[e];
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= H) break;
+                    const uint8_t *q = rgb + 3 * ((long)qy * W + qx);
+                    const uint8_t *qprev = rgb + 3 * ((long)(qy - ey[e]) * W + (qx - ex[e]));
+                    if (dc_max(q, p) >= tau1) break;
+                    if (dc_max(q, qprev) >= tau1) break;
+                    if (j > L2 && dc_max(q, p) >= tau2) break;
+                    k = j;
+                }
+                arms[4 * ((long)y * W + x) + e] = (uint8_t)k;
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------- cost */
+typedef struct {
+    double lambda_ad, lambda_census, gamma_l, eps;
+} orc_cost_params;
+
+/* Eq. 1: adaptive weight from the shortest arm */
+double orc_alpha(int lmin, double gamma_l, double eps)
+{
+    return 1.0 - exp(-gamma_l / ((double)lmin + eps));
+}
+
+/* Eq. 1: robust exponential combination of the AD and census measures.
+ * ad_sum = |dR| + |dG| + |dB|, ham = Hamming distance. */
+double orc_cost_terms(int ad_sum, int ham, int lmin, double lambda_ad, double lambda_census,
+                      double gamma_l, double eps)
+{
+    double alpha = orc_alpha(lmin, gamma_l, eps);
+    double c_ad = (double)ad_sum / 3.0;
+    double c_census = (double)ham;
+    return alpha * (1.0 - exp(-c_ad / lambda_ad)) +
+           (1.0 - alpha) * (1.0 - exp(-c_census / lambda_census));
+}
+
+typedef struct {
+    int W, H, D;
+    const uint8_t *ref_rgb, *oth_rgb;   /* reference view and the other view */
+    const uint64_t *ref_cen, *oth_cen;
+    const uint8_t *ref_arms;
+    int sign;                           /* -1: left reference (q = p - d); +1: right */
+    orc_cost_params cp;
+} view_ctx;
+
+static int lmin_of(const uint8_t *a)
+{
+    int m = a[0];
+    for (int e = 1; e < 4; e++) if (a[e] < m) m = a[e];
+    return m;
+}
+
+/* raw cost C(p, d) of Eq. 1 for the reference pixel (x, y) */
+static double pixel_cost(const view_ctx *v, int x, int y, int d)
+{
+    int xo = x + v->sign * d;
+    if (xo < 0 || xo >= v->W) return 1.0;
+    long ip = (long)y * v->W + x, io = (long)y * v->W + xo;
+    const uint8_t *a = v->ref_rgb + 3 * ip, *b = v->oth_rgb + 3 * io;
+    int ad = abs((int)a[0] - (int)b[0]) + abs((int)a[1] - (int)b[1]) + abs((int)a[2] - (int)b[2]);
+    int ham = orc_hamming(v->ref_cen[ip], v->oth_cen[io]);
+    int lmin = lmin_of(v->ref_arms + 4 * ip);
+    return orc_cost_terms(ad, ham, lmin, v->cp.lambda_ad, v->cp.lambda_census,
+                          v->cp.gamma_l, v->cp.eps);
+}
+
+/* Eq. 2 support-region size N of pixel (x, y) */
+static long region_size(const view_ctx *v, int x, int y)
+{
+    const uint8_t *ap = v->ref_arms + 4 * ((long)y * v->W + x);
+    long n = 0;
+    for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {
+        const uint8_t *aq = v->ref_arms + 4 * ((long)yy * v->W + x);
+        n += (long)aq[0] + aq[1] + 1;
+    }
+    return n;
+}
+
+/*
+ * Aggregated cost (Eq. 2), WTA (Eq. 3) for one view, rows [y0, y1).
+ * For each d the raw costs of rows [y0-L1, y1+L1) are evaluated, the
+ * horizontal segment sums S_H formed by explicit summation, then the
+ * vertical sums of S_H over the vertical arm, divided by N.
+ * Outputs per pixel of the row range: disparity, best and second-best
+ * aggregated cost; optionally the whole aggregated volume [d][y-y0][x].
+ */
+static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
+                    double *best, double *second, double *vol)
+{
+    int W = v->W, H = v->H;
+    int ya = y0 - reach < 0 ? 0 : y0 - reach;
+    int yb = y1 + reach > H ? H : y1 + reach;
+    int nr = yb - ya, no = y1 - y0;
+    double *C = (double *)malloc(sizeof(double) * (size_t)W * nr);
+    double *SH = (double *)malloc(sizeof(double) * (size_t)W * nr);
+    long *N = (long *)malloc(sizeof(long) * (size_t)W * no);
+    if (!C || !SH || !N) { free(C); free(SH); free(N); return ORC_ENOMEM; }
+    for (int y = y0; y < y1; y++)
+        for (int x = 0; x < W; x++) N[(long)(y - y0) * W + x] = region_size(v, x, y);
+    for (long i = 0; i < (long)W * no; i++) { best[i] = INFINITY; second[i] = INFINITY; disp[i] = 0; }
+
+    for (int d = 0; d < v->D; d++) {
+#pragma omp parallel for schedule(static)
+        for (int y = ya; y < yb; y++)
+            for (int x = 0; x < W; x++) C[(long)(y - ya) * W + x] = pixel_cost(v, x, y, d);
+#pragma omp parallel for schedule(static)
+        for (int y = ya; y < yb; y++) {
+            for (int x = 0; x < W; x++) {
+                const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
+                double s = 0.0;
+                for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += C[(long)(y - ya) * W + xx];
+                SH[(long)(y - ya) * W + x] = s;
+            }
+        }
+#pragma omp parallel for schedule(static)
+        for (int y = y0; y < y1; y++) {
+            for (int x = 0; x < W; x++) {
+                const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
+                double s = 0.0;
+                for (int yy = y - a[2]; yy <= y + a[3]; yy++) s += SH[(long)(yy - ya) * W + x];
+                long i = (long)(y - y0) * W + x;
+                double cbar = s / (double)N[i];
+                if (vol) vol[(long)d * W * no + i] = cbar;
+                if (cbar < best[i]) { second[i] = best[i]; best[i] = cbar; disp[i] = (int16_t)d; }
+                else if (cbar < second[i]) { second[i] = cbar; }
+            }
+        }
+    }
+    free(C); free(SH); free(N);
+    return ORC_OK;
+}
+
+/* Left-right consistency check on rows of width W (outlier removal, Sect. 4.3). */
+int orc_lr_check(const int16_t *dl, const int16_t *dr, int W, int rows, int tol, int16_t *out)
+{
+    if (!dl || !dr || !out || W < 1 || rows < 0) return ORC_EINVAL;
+    for (int y = 0; y < rows; y++) {
+        for (int x = 0; x < W; x++) {
+            long i = (long)y * W + x;
+            int d = dl[i];
+            int16_t r = -1;
+            if (tol < 0) r = (int16_t)d;
+            else if (d >= 0 && x - d >= 0) {
+                int d2 = dr[(long)y * W + (x - d)];
+                if (d2 >= 0 && abs(d - d2) <= tol) r = (int16_t)d;
+            }
+            out[i] = r;
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * Full matcher on rows [y0, y1) of a W x H pair with D disparities.
+ * Every output array holds (y1 - y0) x W values; vol_l / vol_r (optional)
+ * hold D x (y1 - y0) x W aggregated costs.  Census and arms are computed on
+ * the whole image (they are cheap next to the aggregation).
+ */
+int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
+              double lambda_ad, double lambda_census, double gamma_l, double eps,
+              int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol,
+              int y0, int y1,
+              int16_t *disp_l, int16_t *disp_r, int16_t *disp_final,
+              double *best_l, double *second_l, double *best_r, double *second_r,
+              double *vol_l, double *vol_r)
+{
+    if (!left || !right || W < 1 || H < 1 || D < 1 || y0 < 0 || y1 > H || y0 > y1) return ORC_EINVAL;
+    if (!disp_l || !disp_r || !disp_final || !best_l || !second_l || !best_r || !second_r)
+        return ORC_EINVAL;
+    size_t npx = (size_t)W * H;
+    uint64_t *cl = (uint64_t *)malloc(8 * npx), *cr = (uint64_t *)malloc(8 * npx);
+    uint8_t *al = (uint8_t *)malloc(4 * npx), *ar = (uint8_t *)malloc(4 * npx);
+    int rc = ORC_ENOMEM;
+    if (!cl || !cr || !al || !ar) goto done;
+    if ((rc = orc_census(left, W, H, cw, ch, cl)) != ORC_OK) goto done;
+    if ((rc = orc_census(right, W, H, cw, ch, cr)) != ORC_OK) goto done;
+    if ((rc = orc_arms(left, W, H, L1, L2, tau1, tau2, al)) != ORC_OK) goto done;
+    if ((rc = orc_arms(right, W, H, L1, L2, tau1, tau2, ar)) != ORC_OK) goto done;
+    {
+        orc_cost_params cp = {lambda_ad, lambda_census, gamma_l, eps};
+        view_ctx vl = {W, H, D, left, right, cl, cr, al, -1, cp};
+        view_ctx vr = {W, H, D, right, left, cr, cl, ar, +1, cp};
+        if ((rc = run_view(&vl, y0, y1, L1, disp_l, best_l, second_l, vol_l)) != ORC_OK) goto done;
+        if ((rc = run_view(&vr, y0, y1, L1, disp_r, best_r, second_r, vol_r)) != ORC_OK) goto done;
+        rc = orc_lr_check(disp_l, disp_r, W, y1 - y0, lr_tol, disp_final);
+    }
+done:
+    free(cl); free(cr); free(al); free(ar);
+    return rc;
+}

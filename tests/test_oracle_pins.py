@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formula: each checks a closed form at a
+point, an invariant, a special case that reduces to a textbook or library
+routine, or a brute-force re-derivation on tiny inputs, chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign or index, a
+swapped view, a transposed bit order) fails at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import oracle as O
+from paper_2203_02300_gb300 import scenes
+
+P = O.Params()
+
+
+def grey_image(v):
+    v = np.asarray(v, np.uint8)
+    return np.repeat(v[:, :, None], 3, axis=2)
+
+
+# ----------------------------------------------------------------- grey
+def test_grey_closed_forms():
+    img = np.array([[[255, 255, 255], [0, 0, 0], [255, 0, 0], [0, 255, 0], [0, 0, 255]]], np.uint8)
+    # (77*255+128)>>8 = 77, (150*255+128)>>8 = 149, (29*255+128)>>8 = 29
+    assert O.grey(img).tolist() == [[255, 0, 77, 149, 29]]
+
+
+def test_grey_matches_bt601_luma_within_one():
+    rng = np.random.default_rng(1)
+    img = rng.integers(0, 256, (37, 53, 3), dtype=np.uint8)
+    f = img.astype(np.float64)
+    luma = 0.299 * f[..., 0] + 0.587 * f[..., 1] + 0.114 * f[..., 2]
+    assert np.abs(O.grey(img) - luma).max() <= 1.0
+
+
+def test_grey_of_neutral_pixels_is_identity():
+    v = np.arange(256, dtype=np.uint8).reshape(16, 16)
+    assert (O.grey(grey_image(v)) == v).all()
+
+
+# --------------------------------------------------------------- census
+def test_census_constant_image_is_zero():
+    for c in (0, 17, 255):
+        img = np.full((11, 13, 3), c, np.uint8)
+        assert (O.census(img) == 0).all()
+
+
+def _kindex(dy, dx, cw=9, ch=7):
+    """Bit position of window offset (dy, dx): rows top to bottom, columns left
+    to right, centre skipped."""
+    k = (dy + ch // 2) * cw + (dx + cw // 2)
+    return k - 1 if (dy, dx) > (0, 0) else k
+
+
+def test_census_ramp_sets_exactly_the_earlier_half():
+    # Y = 12*y + x: a neighbour is darker iff it comes before p in row-major
+    # order, so the interior census is the 31 low bits.
+    H, W = 14, 20
+    v = 12 * np.arange(H)[:, None] + np.arange(W)[None, :]
+    c = O.census(grey_image(v))
+    interior = c[3:H - 3, 4:W - 4]
+    assert (interior == np.uint64((1 << 31) - 1)).all()
+    # top-left: every clamped neighbour is >= p -> no bit; bottom-right:
+    # the 19 offsets with dy >= 0 and dx >= 0 clamp onto p itself.
+    assert int(c[0, 0]) == 0
+    assert bin(int(c[H - 1, W - 1])).count("1") == 62 - 19
+
+
+def test_census_dark_impulse_gives_one_bit_at_its_offset():
+    H, W = 15, 17
+    v = np.full((H, W), 200, np.uint8)
+    y0, x0 = 7, 8
+    v[y0, x0] = 10
+    c = O.census(grey_image(v))
+    for y in range(H):
+        for x in range(W):
+            dy, dx = y0 - y, x0 - x
+            if (y, x) == (y0, x0):
+                assert int(c[y, x]) == 0
+            elif abs(dy) <= 3 and abs(dx) <= 4:
+                assert int(c[y, x]) == 1 << _kindex(dy, dx), (y, x)
+            else:
+                assert int(c[y, x]) == 0
+
+
+def test_census_bright_impulse_sets_all_62_bits():
+    v = np.zeros((9, 11), np.uint8)
+    v[4, 5] = 200
+    c = O.census(grey_image(v))
+    assert int(c[4, 5]) == (1 << 62) - 1
+    c2 = c.copy()
+    c2[4, 5] = 0
+    assert (c2 == 0).all()
+
+
+def test_census_invariant_under_monotone_grey_map():
+    rng = np.random.default_rng(3)
+    v = rng.integers(0, 128, (23, 29), dtype=np.uint8)
+    assert (O.census(grey_image(v)) == O.census(grey_image(2 * v + 1))).all()
+
+
+def test_hamming_counts_bits():
+    rng = np.random.default_rng(4)
+    for a, b in rng.integers(0, 2 ** 63, (200, 2), dtype=np.int64):
+        a, b = int(a) * 2 + 1, int(b)
+        assert O.hamming(a, b) == bin(a ^ b).count("1")
+
+
+# ----------------------------------------------------------------- arms
+def brute_arm(img, x, y, ex, ey, p):
+    """Largest k for which ALL of the double-threshold conditions hold for
+    every j <= k, checked from scratch for each candidate k."""
+    H, W, _ = img.shape
+    f = img.astype(int)
+    best = 0
+    for k in range(1, p.arm_l1 + 1):
+        ok = True
+        for j in range(1, k + 1):
+            qx, qy = x + j * ex, y + j * ey
+            if not (0 <= qx < W and 0 <= qy < H):
+                ok = False
+                break
+            dp = np.abs(f[qy, qx] - f[y, x]).max()
+            dn = np.abs(f[qy, qx] - f[qy - ey, qx - ex]).max()
+            if dp >= p.tau1 or dn >= p.tau1 or (j > p.arm_l2 and dp >= p.tau2):
+                ok = False
+                break
+        if ok:
+            best = k
+    return best
+
+
+def test_arms_match_brute_force_on_blocky_images():
+    rng = np.random.default_rng(5)
+    p = O.Params(arm_l1=7, arm_l2=3, tau1=20, tau2=6)
+    for trial in range(3):
+        base = rng.integers(0, 256, (4, 5, 3))
+        img = np.kron(base, np.ones((4, 4, 1))).astype(np.int64)
+        img = np.clip(img + rng.integers(-6, 7, img.shape), 0, 255).astype(np.uint8)
+        a = O.arms(img, p)
+        H, W, _ = img.shape
+        for y in range(H):
+            for x in range(W):
+                for e, (ex, ey) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+                    assert a[y, x, e] == brute_arm(img, x, y, ex, ey, p), (trial, y, x, e)
+
+
+def test_arms_constant_image_reach_border_or_l1():
+    H, W = 50, 90
+    img = np.full((H, W, 3), 90, np.uint8)
+    a = O.arms(img, P).astype(int)
+    ys, xs = np.mgrid[0:H, 0:W]
+    L1 = P.arm_l1
+    assert (a[..., 0] == np.minimum(L1, xs)).all()
+    assert (a[..., 1] == np.minimum(L1, W - 1 - xs)).all()
+    assert (a[..., 2] == np.minimum(L1, ys)).all()
+    assert (a[..., 3] == np.minimum(L1, H - 1 - ys)).all()
+
+
+def test_arms_stop_at_stripe_edges():
+    H, W, s = 9, 40, 5
+    cols = (np.arange(W) // s) % 2 * 200
+    img = np.repeat(np.repeat(cols[None, :, None], H, 0), 3, 2).astype(np.uint8)
+    a = O.arms(img, P).astype(int)
+    xs = np.arange(W)
+    assert (a[:, :, 0] == (xs % s)[None]).all()
+    assert (a[:, :, 1] == (s - 1 - xs % s)[None]).all()
+
+
+def test_arms_second_threshold_applies_beyond_l2():
+    # a slow ramp (step 1 per pixel): Dc(p_j, p) = j, so with tau2 = 6 the arm
+    # can pass L2 only while j < 6; with L2 >= L1 the rule is single-threshold.
+    W = 60
+    v = np.clip(np.arange(W), 0, 255)
+    img = grey_image(np.repeat(v[None, :], 3, 0))
+    p = O.Params(arm_l1=30, arm_l2=3, tau1=20, tau2=6)
+    a = O.arms(img, p)
+    assert a[1, 0, 1] == 5            # j=4,5 beyond L2 pass (4,5 < 6), j=6 fails
+    p2 = O.Params(arm_l1=30, arm_l2=30, tau1=20, tau2=6)
+    assert O.arms(img, p2)[1, 0, 1] == 19   # tau1: Dc = j < 20
+
+
+# ------------------------------------------------------------ Eq. 1 cost
+def _eq1_exact(ad_sum, ham, lmin):
+    """Eq. 1 evaluated symbolically at the Sect. 7.2 parameters (40 digits)."""
+    g, e, lad, lc = sympy.Integer(1), sympy.Rational(4, 5), sympy.Integer(10), sympy.Integer(40)
+    alpha = 1 - sympy.exp(-g / (lmin + e))
+    c = alpha * (1 - sympy.exp(-sympy.Rational(ad_sum, 3) / lad)) + \
+        (1 - alpha) * (1 - sympy.exp(-sympy.Integer(ham) / lc))
+    return float(sympy.N(c, 40)), float(sympy.N(alpha, 40))
+
+
+@pytest.mark.parametrize("ad,ham,lmin", [(0, 0, 0), (30, 0, 0), (0, 40, 34), (765, 62, 3),
+                                         (1, 1, 17), (90, 13, 5)])
+def test_eq1_closed_form_points(ad, ham, lmin):
+    c, a = _eq1_exact(ad, ham, lmin)
+    assert O.cost_terms(ad, ham, lmin) == pytest.approx(c, rel=1e-14, abs=1e-15)
+    assert O.alpha(lmin) == pytest.approx(a, rel=1e-14)
+
+
+def test_alpha_shrinks_as_arms_grow():
+    # Sect. 4.2.1: a longer shortest arm means weaker texture and a smaller
+    # weight on the AD measure.
+    a = [O.alpha(l) for l in range(0, 35)]
+    assert all(0.0 < x < 1.0 for x in a)
+    assert all(a[i] > a[i + 1] for i in range(34))
+
+
+def test_eq1_bounds_and_monotonicity():
+    assert O.cost_terms(0, 0, 5) == 0.0
+    assert O.cost_terms(765, 62, 0) < 1.0
+    for lmin in (0, 4, 34):
+        row = [O.cost_terms(ad, 7, lmin) for ad in range(0, 766, 15)]
+        assert all(row[i] < row[i + 1] for i in range(len(row) - 1))
+        col = [O.cost_terms(20, h, lmin) for h in range(63)]
+        assert all(col[i] < col[i + 1] for i in range(62))
+
+
+def test_eq1_weight_limits():
+    # gamma_L -> large: alpha -> 1, only the AD term remains;
+    # gamma_L -> 0: alpha -> 0, only the census term remains.
+    big = O.Params(gamma_l=1e6)
+    small = O.Params(gamma_l=1e-12)
+    assert O.cost_terms(30, 50, 3, big) == pytest.approx(1 - np.exp(-1.0), rel=1e-9)
+    assert O.cost_terms(30, 40, 3, small) == pytest.approx(1 - np.exp(-1.0), rel=1e-9)
+
+
+# ----------------------------------------------------- Eq. 2 aggregation
+def _region(arms_img, x, y):
+    """N_p as an explicit coordinate set: for every q on p's vertical arm,
+    the pixels of q's own horizontal segment."""
+    l, r, u, d = (int(v) for v in arms_img[y, x])
+    pts = set()
+    for yy in range(y - u, y + d + 1):
+        ql, qr = int(arms_img[yy, x, 0]), int(arms_img[yy, x, 1])
+        for xx in range(x - ql, x + qr + 1):
+            pts.add((xx, yy))
+    return pts
+
+
+def _raw_costs_left(left, right, D, p):
+    H, W, _ = left.shape
+    cl, cr = O.census(left), O.census(right)
+    al = O.arms(left, p)
+    lmin = al.min(axis=2)
+    C = np.ones((D, H, W))
+    li = left.astype(int)
+    ri = right.astype(int)
+    for d in range(D):
+        for y in range(H):
+            for x in range(d, W):
+                ad = int(np.abs(li[y, x] - ri[y, x - d]).sum())
+                ham = bin(int(cl[y, x]) ^ int(cr[y, x - d])).count("1")
+                C[d, y, x] = O.cost_terms(ad, ham, int(lmin[y, x]), p)
+    return C, al
+
+
+def test_aggregation_equals_brute_force_region_mean():
+    rng = np.random.default_rng(6)
+    base = rng.integers(0, 256, (3, 4, 3))
+    left = np.clip(np.kron(base, np.ones((4, 4, 1))) + rng.integers(-8, 9, (12, 16, 3)),
+                   0, 255).astype(np.uint8)
+    right = np.roll(left, -2, axis=1)
+    right[:, -2:] = rng.integers(0, 256, (12, 2, 3))
+    p = O.Params(arm_l1=5, arm_l2=2)
+    D = 5
+    res = O.match(left, right, D, p, volume=True)
+    C, al = _raw_costs_left(left, right, D, p)
+    for y in range(12):
+        for x in range(16):
+            pts = _region(al, x, y)
+            for d in range(D):
+                ref = sum(C[d, yy, xx] for xx, yy in pts) / len(pts)
+                assert res.vol_l[d, y, x] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+
+
+def test_aggregation_box_special_case_matches_integral_image():
+    # With no colour stop (tau = 256) and L2 = L1 = r, arms are the clipped
+    # r-box, so Eq. 2 is a clipped box mean, computed here by cumulative sums.
+    rng = np.random.default_rng(7)
+    H, W, D, r = 20, 26, 4, 3
+    left = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    right = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    p = O.Params(arm_l1=r, arm_l2=r, tau1=256, tau2=256)
+    res = O.match(left, right, D, p, volume=True)
+    C, _ = _raw_costs_left(left, right, D, p)
+    for d in range(D):
+        S = np.zeros((H + 1, W + 1))
+        S[1:, 1:] = C[d].cumsum(0).cumsum(1)
+        for y in range(H):
+            for x in range(W):
+                y0, y1, x0, x1 = max(0, y - r), min(H, y + r + 1), max(0, x - r), min(W, x + r + 1)
+                box = S[y1, x1] - S[y0, x1] - S[y1, x0] + S[y0, x0]
+                n = (y1 - y0) * (x1 - x0)
+                assert res.vol_l[d, y, x] == pytest.approx(box / n, rel=1e-12, abs=1e-14)
+
+
+# ----------------------------------------------------------- Eq. 3 WTA
+def test_identical_views_give_zero_disparity():
+    rng = np.random.default_rng(8)
+    img = scenes._texture(rng, 40, 48)
+    img = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    res = O.match(img, img, 12)
+    assert (res.disp_l == 0).all() and (res.disp_r == 0).all()
+    assert (res.best_l == 0).all() and (res.best_r == 0).all()
+    assert (res.disp == 0).all()
+
+
+def test_all_tied_costs_take_the_smallest_disparity():
+    img = np.full((16, 60, 3), 77, np.uint8)
+    D = 6
+    res = O.match(img, img, D, O.Params(arm_l1=3, arm_l2=3))
+    # away from the left border every in-range candidate costs exactly 0
+    assert (res.disp_l[:, 3 + D:] == 0).all()
+    assert (res.best_l[:, 3 + D:] == 0).all() and (res.second_l[:, 3 + D:] == 0).all()
+
+
+def _interior_mask(gt, occ, margin):
+    H, W = gt.shape
+    edge = np.zeros_like(occ)
+    edge[:, 1:] |= gt[:, 1:] != gt[:, :-1]
+    edge[1:, :] |= gt[1:, :] != gt[:-1, :]
+    bad = edge | occ
+    from scipy import ndimage
+    near = ndimage.binary_dilation(bad, iterations=margin)
+    m = ~near
+    m[:margin] = m[-margin:] = False
+    m[:, :margin] = m[:, -margin:] = False
+    return m
+
+
+def test_wta_recovers_ground_truth_in_textured_plane_interiors():
+    s = scenes.config_scene(1)
+    res = O.match(s.left, s.right, s.D)
+    gt = np.rint(s.disp).astype(np.int16)
+    m = _interior_mask(gt, s.occluded, P.arm_l1 + 4)
+    assert m.sum() > 5000
+    acc = (res.disp_l[m] == gt[m]).mean()
+    assert acc >= 0.99, acc
+
+
+# -------------------------------------------------------- LR check
+def test_lr_check_hand_cases():
+    dl = np.array([[0, 1, 2, 2, 5, 1]], np.int16)
+    dr = np.array([[0, 3, 0, 9, 2, 4]], np.int16)
+    # x=0: d=0 -> dr[0]=0 ok; x=1: d=1 -> dr[0]=0 |1-0|<=1 ok; x=2: d=2 -> dr[0]=0 bad;
+    # x=3: d=2 -> dr[1]=3 ok; x=4: d=5 -> x-d<0 bad; x=5: d=1 -> dr[4]=2 ok
+    assert O.lr_check(dl, dr, 1).tolist() == [[0, 1, -1, 2, -1, 1]]
+    assert O.lr_check(dl, dr, 0).tolist() == [[0, -1, -1, -1, -1, -1]]
+    assert O.lr_check(dl, dr, -1).tolist() == dl.tolist()
+
+
+def test_mirror_swap_symmetry():
+    # Swapping the views and mirroring both rows turns the right-reference
+    # problem into the left-reference one: d_L' = mirror(d_R), d_R' = mirror(d_L).
+    s = scenes.plane_scene(96, 40, 16, 4, seed=11, drange=(2, 12), noise_sigma=1.0)
+    a = O.match(s.left, s.right, s.D)
+    b = O.match(s.right[:, ::-1], s.left[:, ::-1], s.D)
+    assert (b.disp_l == a.disp_r[:, ::-1]).all()
+    assert (b.disp_r == a.disp_l[:, ::-1]).all()
+    assert np.allclose(b.best_l, a.best_r[:, ::-1], rtol=1e-12, atol=0)
+    assert (b.disp == O.lr_check(b.disp_l, b.disp_r, 1)).all()
+
+
+def test_row_window_equals_full_run():
+    s = scenes.config_scene(1)
+    full = O.match(s.left, s.right, s.D)
+    part = O.match(s.left, s.right, s.D, rows=(100, 140))
+    assert (part.disp_l == full.disp_l[100:140]).all()
+    assert (part.disp_r == full.disp_r[100:140]).all()
+    assert (part.best_l == full.best_l[100:140]).all()
