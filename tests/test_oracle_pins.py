@@ -374,3 +374,29 @@ def test_row_window_equals_full_run():
     assert (part.disp_l == full.disp_l[100:140]).all()
     assert (part.disp_r == full.disp_r[100:140]).all()
     assert (part.best_l == full.best_l[100:140]).all()
+
+
+def test_arms_consecutive_colour_rule():
+    # Each step differs from p by only 10 but from its predecessor by 20 at
+    # j = 2: the neighbour-to-neighbour condition alone stops the arm there.
+    row = np.array([100] + [110, 90] * 20, np.int64)
+    img = grey_image(np.repeat(row[None, :], 3, 0).astype(np.uint8))
+    a = O.arms(img, P)
+    assert a[1, 0, 1] == 1
+    # without the jump (110, 110, ...) only the L2/tau2 rule stops it
+    row2 = np.array([100] + [110] * 40, np.int64)
+    a2 = O.arms(grey_image(np.repeat(row2[None, :], 3, 0).astype(np.uint8)), P)
+    assert a2[1, 0, 1] == P.arm_l2
+
+
+def test_arms_brute_force_with_strong_noise():
+    rng = np.random.default_rng(15)
+    p = O.Params(arm_l1=6, arm_l2=2, tau1=20, tau2=9)
+    base = rng.integers(0, 256, (3, 4, 3))
+    img = np.kron(base, np.ones((4, 4, 1))).astype(np.int64)
+    img = np.clip(img + rng.integers(-12, 13, img.shape), 0, 255).astype(np.uint8)
+    a = O.arms(img, p)
+    for y in range(img.shape[0]):
+        for x in range(img.shape[1]):
+            for e, (ex, ey) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+                assert a[y, x, e] == brute_arm(img, x, y, ex, ey, p), (y, x, e)
