@@ -1,0 +1,234 @@
+/*
+ * dco_stereo.h -- C ABI of the GB300 (sm_103a) AD-census stereo matcher.
+ *
+ * The matcher is the sparse-depth stage of the depth contour occlusion
+ * method of arXiv 2203.02300 ("Mixed Reality Depth Contour Occlusion Using
+ * Binocular Similarity Matching and Three-dimensional Contour
+ * Optimisation"), Sect. 4: a rectified RGB pair goes in, a sparse disparity
+ * map comes out.  Steps: census transform and AD measure (Sect. 4.2.1),
+ * cross-support arms (Sect. 4.1), the robust exponential AD+census cost with
+ * the adaptive weight alpha (Eq. 1), aggregation over the adaptive filter
+ * area (Eq. 2), winner-take-all (Eq. 3) and outlier removal by a left-right
+ * consistency check (Sect. 4.3, Sect. 7.4).
+ *
+ * Conventions shared by every entry point
+ *   - Images are interleaved RGB uint8, row-major, pitch 3*W bytes, no
+ *     padding (pixel (x, y) channel c at byte 3*(y*W + x) + c).
+ *   - Disparities are int16, row-major W*H, d in [0, D-1]; -1 = invalid
+ *     (rejected by the consistency check).
+ *   - "device" pointers must be CUDA device memory (or managed memory) of
+ *     the device the handle was created on; "host" pointers are ordinary
+ *     (preferably pinned) host memory.  The caller owns every buffer it
+ *     passes; the library never frees or retains them after the call.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL =
+ *     the legacy default stream) and returns before it completes, except
+ *     where stated.  Output buffers are valid once the stream reaches the
+ *     call's completion.
+ *   - A handle owns one workspace.  Calls on one handle must not run
+ *     concurrently (use one handle per stream that works in parallel).
+ *   - Argument errors return DCO_EINVAL before anything is enqueued.
+ *     Limits: 1 <= W, H <= 16384; 1 <= D <= 256; D <= W; 1 <= arm_l1 <= 40;
+ *     census window odd, at most 64 bits; lambda_ad, lambda_census, eps > 0;
+ *     gamma_l >= 0.
+ *   - Device-side failures (an internal bound check) do not trap: they set
+ *     the handle's status word, read with dco_stereo_sync_status().
+ */
+#ifndef DCO_STEREO_H
+#define DCO_STEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dco_stereo dco_stereo; /* opaque handle: device, workspace, tables */
+typedef void *dco_stream;             /* cudaStream_t */
+
+typedef enum {
+    DCO_OK = 0,
+    DCO_EINVAL = 1,   /* bad argument (size, pointer, parameter) */
+    DCO_ENOMEM = 2,   /* device allocation failed */
+    DCO_EBUDGET = 3,  /* the call needs more workspace than the handle's budget */
+    DCO_ECUDA = 4,    /* a CUDA runtime call failed */
+    DCO_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    DCO_EDEVICE = 6   /* a kernel reported an internal bound-check failure */
+} dco_status;
+
+/*
+ * Matcher parameters.  lambda_ad, lambda_census, gamma_l, eps are the
+ * paper's (Eq. 1; values of Sect. 7.2: 10, 40, 1, 0.8).  The census window,
+ * the arm rule constants and the consistency tolerance are not given in the
+ * paper; the defaults are this library's reading:
+ *   census 9x7 on the grey level Y = (77R + 150G + 29B + 128) >> 8, centre
+ *   excluded, clamp-to-edge, bit k = [Y(neighbour) < Y(p)] in window
+ *   row-major order;
+ *   arms (Sect. 4.1, colour + distance double threshold): the arm in one
+ *   direction is the largest k <= arm_l1 such that every step j <= k stays in
+ *   the image, has max-channel difference < tau1 to p and to step j-1, and,
+ *   when j > arm_l2, < tau2 to p (defaults 34, 17, 20, 6);
+ *   lr_tol = 1 (a negative value disables the consistency check).
+ */
+typedef struct {
+    float lambda_ad;
+    float lambda_census;
+    float gamma_l;
+    float eps;
+    int census_w;
+    int census_h;
+    int arm_l1;
+    int arm_l2;
+    int tau1;
+    int tau2;
+    int lr_tol;
+    int d_chunk; /* disparities aggregated per pass (0 = automatic); see dco_stereo_match */
+} dco_params;
+
+/* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */
+dco_status dco_params_default(dco_params *p);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *dco_status_string(dco_status s);
+
+/*
+ * Create a handle on CUDA device `device`.  `workspace_budget_bytes` caps
+ * the device memory the handle may allocate for its workspace (0 = no
+ * cap).  The workspace grows on demand (a synchronising reallocation) or is
+ * sized up front by dco_stereo_reserve().  *out is NULL on failure.
+ */
+dco_status dco_stereo_create(dco_stereo **out, int device, size_t workspace_budget_bytes);
+
+/* Release the handle and its workspace.  NULL is accepted.  Synchronises
+ * the device before freeing. */
+void dco_stereo_destroy(dco_stereo *h);
+
+/*
+ * Device bytes of workspace one match of a W x H pair with D disparities
+ * needs under params p (0 if the arguments are invalid).  Per pixel: two
+ * 16-byte census/colour records, two arm words, the running best cost and
+ * disparity of both views; per pixel and per disparity of one pass: the
+ * two horizontal-aggregate slices (4 bytes each).  Never the full
+ * W x H x D cost volume.
+ */
+size_t dco_stereo_workspace_bytes(int W, int H, int D, const dco_params *p);
+
+/* Allocate the workspace for (W, H, D, p) now.  DCO_EBUDGET if it exceeds
+ * the handle's budget. */
+dco_status dco_stereo_reserve(dco_stereo *h, int W, int H, int D, const dco_params *p);
+
+/*
+ * The whole hot path for one rectified pair (Sect. 4.1-4.3):
+ *   census + grey + arms for both views -> Eq. 1 costs -> Eq. 2 horizontal
+ *   then vertical aggregation over the cross-support region -> Eq. 3 WTA
+ *   for the left- and right-reference views -> left-right check.
+ * left, right: device, W*H*3 bytes.  disp_out: device, W*H int16.
+ * The disparity range is processed in passes of p->d_chunk disparities
+ * (automatic when 0) so the workspace holds slices, never the volume.
+ * p = NULL uses the defaults.
+ */
+dco_status dco_stereo_match(dco_stereo *h, const uint8_t *left, const uint8_t *right,
+                            int W, int H, int D, const dco_params *p,
+                            int16_t *disp_out, dco_stream stream);
+
+/*
+ * As dco_stereo_match, with the per-view results.  Any output may be NULL.
+ *   disp_left / disp_right: device W*H int16, Eq. 3 for the left / right
+ *     reference view before the consistency check;
+ *   cost_left / cost_right: device W*H float, the minimum aggregated cost
+ *     (Eq. 2 value at the chosen disparity).
+ */
+dco_status dco_stereo_match_views(dco_stereo *h, const uint8_t *left, const uint8_t *right,
+                                  int W, int H, int D, const dco_params *p,
+                                  int16_t *disp_out, int16_t *disp_left, int16_t *disp_right,
+                                  float *cost_left, float *cost_right, dco_stream stream);
+
+/*
+ * As dco_stereo_match, with host buffers: copies left/right (host, W*H*3
+ * bytes each) to the handle's device staging buffers, runs the path, copies
+ * the disparity map back into disp_host (host, W*H int16) and waits for the
+ * stream.  Pinned host memory makes the copies asynchronous.
+ */
+dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host,
+                                 const uint8_t *right_host, int W, int H, int D,
+                                 const dco_params *p, int16_t *disp_host, dco_stream stream);
+
+/*
+ * Stage a1 alone (Sect. 4.2.1): census strings of one image.
+ * rgb: device W*H*3 bytes.  census_out: device W*H uint64 (bits above
+ * census_w*census_h-2 are zero).
+ */
+dco_status dco_stereo_census(dco_stereo *h, const uint8_t *rgb, int W, int H,
+                             const dco_params *p, uint64_t *census_out, dco_stream stream);
+
+/*
+ * Stage a2 alone (Sect. 4.1): the four arm lengths of one image.
+ * arms_out: device W*H*4 bytes, per pixel {left, right, up, down}.
+ */
+dco_status dco_stereo_arms(dco_stereo *h, const uint8_t *rgb, int W, int H,
+                           const dco_params *p, uint8_t *arms_out, dco_stream stream);
+
+/*
+ * Eq. 2 aggregated costs of one reference view for every disparity
+ * (diagnostic; materialises the volume).  view 0 = left reference
+ * (match q = p - d), 1 = right reference (match q = p + d).
+ * vol_out: device D*H*W float, index (d*H + y)*W + x.
+ */
+dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint8_t *right,
+                                  int W, int H, int D, const dco_params *p, int view,
+                                  float *vol_out, dco_stream stream);
+
+/*
+ * Stage a7 alone: left-right consistency.  out(x,y) = dl(x,y) if
+ * x - dl >= 0 and |dl - dr(x - dl, y)| <= tol, else -1; tol < 0 copies dl.
+ * dl, dr, out: device W*H int16.  The handle is only used for its device.
+ */
+dco_status dco_stereo_lr_check(dco_stereo *h, const int16_t *dl, const int16_t *dr,
+                               int W, int H, int tol, int16_t *out, dco_stream stream);
+
+/* One pair of a batch (all pointers device). */
+typedef struct {
+    const uint8_t *left;
+    const uint8_t *right;
+    int W, H, D;
+    int16_t *disp_out;
+} dco_pair_desc;
+
+/*
+ * Match n independent pairs of possibly different W, H, D in one pass of
+ * the pipeline: each stage is one launch over all pairs.  The workspace
+ * holds all pairs' per-pixel buffers and one pass of slices for each.
+ * Results equal dco_stereo_match on each pair alone (bit-identical).
+ * descs: host array of n descriptors.
+ */
+dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int n,
+                                  const dco_params *p, dco_stream stream);
+
+/*
+ * Waits for all work of the handle's device, then reads and clears the
+ * device status word.  DCO_OK, or DCO_EDEVICE if a kernel reported a failed
+ * internal check since the last call.
+ */
+dco_status dco_stereo_sync_status(dco_stereo *h);
+
+/* Text of the last CUDA or budget error seen by the handle ("" if none).
+ * Owned by the handle, valid until its next call. */
+const char *dco_stereo_last_error(dco_stereo *h);
+
+/*
+ * Per-kernel timing.  When enabled, every kernel the handle launches is
+ * bracketed by CUDA events on its stream.  After the stream has finished,
+ * dco_stereo_profile_get returns, per kernel name, the number of launches
+ * and their summed duration in milliseconds.
+ */
+dco_status dco_stereo_set_profiling(dco_stereo *h, int enable);
+dco_status dco_stereo_profile_reset(dco_stereo *h);
+int dco_stereo_profile_count(dco_stereo *h);
+dco_status dco_stereo_profile_get(dco_stereo *h, int i, const char **name, int *launches,
+                                  double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCO_STEREO_H */

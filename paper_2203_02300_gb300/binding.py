@@ -1,0 +1,272 @@
+"""Thin Python binding of include/dco_stereo.h (ctypes, argument marshalling only).
+
+Every step of the matcher runs in libdco_stereo.so; this module converts
+torch tensors / numpy arrays to pointers and sizes, nothing else.  Method
+names mirror the C entry points: dco_stereo_<name> -> Stereo.<name>.
+
+There is no fallback: if the library is not built, or no CUDA device is
+present, constructing a Stereo raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+c_int, c_float, c_void_p, c_size_t = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+STATUS = {0: "DCO_OK", 1: "DCO_EINVAL", 2: "DCO_ENOMEM", 3: "DCO_EBUDGET", 4: "DCO_ECUDA",
+          5: "DCO_ETIMEOUT", 6: "DCO_EDEVICE"}
+DCO_OK, DCO_EINVAL, DCO_ENOMEM, DCO_EBUDGET, DCO_ECUDA, DCO_ETIMEOUT, DCO_EDEVICE = range(7)
+
+
+class Params(ctypes.Structure):
+    """dco_params; defaults from dco_params_default()."""
+    _fields_ = [("lambda_ad", c_float), ("lambda_census", c_float), ("gamma_l", c_float),
+                ("eps", c_float), ("census_w", c_int), ("census_h", c_int), ("arm_l1", c_int),
+                ("arm_l2", c_int), ("tau1", c_int), ("tau2", c_int), ("lr_tol", c_int),
+                ("d_chunk", c_int)]
+
+    @classmethod
+    def default(cls, **over) -> "Params":
+        p = cls()
+        _check(lib().dco_params_default(ctypes.byref(p)), None)
+        for k, v in over.items():
+            setattr(p, k, v)
+        return p
+
+
+class PairDesc(ctypes.Structure):
+    _fields_ = [("left", c_void_p), ("right", c_void_p), ("W", c_int), ("H", c_int), ("D", c_int),
+                ("disp_out", c_void_p)]
+
+
+class DcoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/dco_stereo.h declares."""
+    text = open(os.path.join(_build.INCLUDE, "dco_stereo.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dco_\w+)\s*\(", text)))
+
+
+def lib():
+    """The loaded libdco_stereo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P = c_void_p
+        sig = {
+            "dco_params_default": (c_int, [P]),
+            "dco_status_string": (ctypes.c_char_p, [c_int]),
+            "dco_stereo_create": (c_int, [P, c_int, c_size_t]),
+            "dco_stereo_destroy": (None, [P]),
+            "dco_stereo_workspace_bytes": (c_size_t, [c_int, c_int, c_int, P]),
+            "dco_stereo_reserve": (c_int, [P, c_int, c_int, c_int, P]),
+            "dco_stereo_match": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P]),
+            "dco_stereo_match_views": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P, P, P, P, P]),
+            "dco_stereo_match_host": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P]),
+            "dco_stereo_census": (c_int, [P, P, c_int, c_int, P, P, P]),
+            "dco_stereo_arms": (c_int, [P, P, c_int, c_int, P, P, P]),
+            "dco_stereo_cost_volume": (c_int, [P, P, P, c_int, c_int, c_int, P, c_int, P, P]),
+            "dco_stereo_lr_check": (c_int, [P, P, P, c_int, c_int, c_int, P, P]),
+            "dco_stereo_match_batch": (c_int, [P, P, c_int, P, P]),
+            "dco_stereo_sync_status": (c_int, [P]),
+            "dco_stereo_last_error": (ctypes.c_char_p, [P]),
+            "dco_stereo_set_profiling": (c_int, [P, c_int]),
+            "dco_stereo_profile_reset": (c_int, [P]),
+            "dco_stereo_profile_count": (c_int, [P]),
+            "dco_stereo_profile_get": (c_int, [P, c_int, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, h) -> None:
+    if code != DCO_OK:
+        detail = ""
+        if h is not None:
+            detail = (lib().dco_stereo_last_error(h) or b"").decode()
+        raise DcoError(code, (lib().dco_status_string(code) or b"").decode() + (f" ({detail})" if detail else ""))
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _rgb_dims(t) -> tuple[int, int]:
+    assert tuple(t.shape[2:]) == (3,), "images are (H, W, 3) uint8"
+    assert t.is_contiguous(), "images must be contiguous"
+    return int(t.shape[1]), int(t.shape[0])
+
+
+class Stereo:
+    """A dco_stereo handle on one CUDA device (owns the workspace)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._h = c_void_p()
+        _check(lib().dco_stereo_create(ctypes.byref(self._h), device, budget_bytes), None)
+        self.device = device
+
+    def close(self) -> None:
+        if self._h:
+            lib().dco_stereo_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- sizing
+    @staticmethod
+    def workspace_bytes(W: int, H: int, D: int, params: Optional[Params] = None) -> int:
+        return int(lib().dco_stereo_workspace_bytes(W, H, D, ctypes.byref(params) if params else None))
+
+    def reserve(self, W: int, H: int, D: int, params: Optional[Params] = None) -> None:
+        _check(lib().dco_stereo_reserve(self._h, W, H, D, ctypes.byref(params) if params else None), self._h)
+
+    # -- the hot path
+    def match(self, left, right, D: int, params: Optional[Params] = None, out=None, stream=None):
+        import torch
+        W, H = _rgb_dims(left)
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.int16, device=left.device)
+        _check(lib().dco_stereo_match(self._h, _ptr(left), _ptr(right), W, H, D,
+                                      ctypes.byref(params) if params else None, _ptr(out),
+                                      _stream(stream)), self._h)
+        return out
+
+    def match_views(self, left, right, D: int, params: Optional[Params] = None, stream=None,
+                    costs: bool = True):
+        import torch
+        W, H = _rgb_dims(left)
+        dev = left.device
+        out = torch.empty((H, W), dtype=torch.int16, device=dev)
+        dl = torch.empty_like(out)
+        dr = torch.empty_like(out)
+        cl = torch.empty((H, W), dtype=torch.float32, device=dev) if costs else None
+        cr = torch.empty((H, W), dtype=torch.float32, device=dev) if costs else None
+        _check(lib().dco_stereo_match_views(self._h, _ptr(left), _ptr(right), W, H, D,
+                                            ctypes.byref(params) if params else None, _ptr(out),
+                                            _ptr(dl), _ptr(dr), _ptr(cl), _ptr(cr), _stream(stream)),
+               self._h)
+        return out, dl, dr, cl, cr
+
+    def match_host(self, left: np.ndarray, right: np.ndarray, D: int,
+                   params: Optional[Params] = None, out: Optional[np.ndarray] = None, stream=None):
+        H, W, _ = left.shape
+        assert left.flags.c_contiguous and right.flags.c_contiguous
+        if out is None:
+            out = np.empty((H, W), np.int16)
+        _check(lib().dco_stereo_match_host(self._h, _ptr(left), _ptr(right), W, H, D,
+                                           ctypes.byref(params) if params else None, _ptr(out),
+                                           _stream(stream)), self._h)
+        return out
+
+    def match_batch(self, pairs: Sequence, params: Optional[Params] = None, stream=None):
+        """pairs: sequence of (left, right, D, out) device tensors."""
+        arr = (PairDesc * len(pairs))()
+        for i, (l, r, D, o) in enumerate(pairs):
+            W, H = _rgb_dims(l)
+            arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o))
+        _check(lib().dco_stereo_match_batch(self._h, arr, len(pairs),
+                                            ctypes.byref(params) if params else None, _stream(stream)),
+               self._h)
+
+    # -- stages
+    def census(self, img, params: Optional[Params] = None, stream=None):
+        import torch
+        W, H = _rgb_dims(img)
+        out = torch.empty((H, W), dtype=torch.int64, device=img.device)
+        _check(lib().dco_stereo_census(self._h, _ptr(img), W, H, ctypes.byref(params) if params else None,
+                                       _ptr(out), _stream(stream)), self._h)
+        return out
+
+    def arms(self, img, params: Optional[Params] = None, stream=None):
+        import torch
+        W, H = _rgb_dims(img)
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=img.device)
+        _check(lib().dco_stereo_arms(self._h, _ptr(img), W, H, ctypes.byref(params) if params else None,
+                                     _ptr(out), _stream(stream)), self._h)
+        return out
+
+    def cost_volume(self, left, right, D: int, view: int, params: Optional[Params] = None, stream=None):
+        import torch
+        W, H = _rgb_dims(left)
+        out = torch.empty((D, H, W), dtype=torch.float32, device=left.device)
+        _check(lib().dco_stereo_cost_volume(self._h, _ptr(left), _ptr(right), W, H, D,
+                                            ctypes.byref(params) if params else None, view, _ptr(out),
+                                            _stream(stream)), self._h)
+        return out
+
+    def lr_check(self, dl, dr, tol: int = 1, stream=None):
+        import torch
+        H, W = dl.shape
+        out = torch.empty_like(dl)
+        _check(lib().dco_stereo_lr_check(self._h, _ptr(dl), _ptr(dr), W, H, tol, _ptr(out),
+                                         _stream(stream)), self._h)
+        return out
+
+    # -- status and profiling
+    def sync_status(self) -> None:
+        _check(lib().dco_stereo_sync_status(self._h), self._h)
+
+    def set_profiling(self, on: bool) -> None:
+        _check(lib().dco_stereo_set_profiling(self._h, 1 if on else 0), self._h)
+
+    def profile_reset(self) -> None:
+        _check(lib().dco_stereo_profile_reset(self._h), self._h)
+
+    def profile(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last reset."""
+        n = lib().dco_stereo_profile_count(self._h)
+        res = {}
+        for i in range(n):
+            name = ctypes.c_char_p()
+            cnt = c_int()
+            ms = ctypes.c_double()
+            _check(lib().dco_stereo_profile_get(self._h, i, ctypes.byref(name), ctypes.byref(cnt),
+                                                ctypes.byref(ms)), self._h)
+            res[name.value.decode()] = (cnt.value, ms.value)
+        return res

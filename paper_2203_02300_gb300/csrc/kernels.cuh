@@ -1,0 +1,93 @@
+// Device-side types and constants of the AD-census matcher (arXiv 2203.02300, Sect. 4).
+//
+// Data layout in HBM (row-major, pixel index i = y*W + x):
+//   rgbx[i]  uint32 r | g<<8 | b<<16           packed colour of the input image
+//   grey[i]  uint8  (77R + 150G + 29B + 128) >> 8
+//   rec[y*rpitch + x]  uint4 {census bits 0-31, census bits 32-63,
+//                    r | g<<8 | b<<16 | Lmin<<24, float bits of alpha(Lmin)*S}
+//                    rows padded by kRPad records on both sides
+//   arms[i]  uchar4 {left, right, up, down}
+//   sh[i*dstride + j]  uint32 horizontal segment sum (fixed point) of
+//                    disparity d0 + j (one pass of the d range)
+//   best[i]  uint64 (aggregate << 32 | d), WTA state carried across passes
+//
+// Costs are carried in unsigned fixed point with scale S (an integer below
+// 2^20, chosen so a full (2*L1+1)^2 region of costs <= 1 stays below 2^32).
+// Prefix sums wrap modulo 2^32, and differences of prefix sums are exact
+// region sums, so the Eq. 2 aggregation is exact integer arithmetic on the
+// rounded per-pixel costs; only the Eq. 1 evaluation (FP32) and the rounding
+// to fixed point differ from the real-valued definition.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dco {
+
+constexpr int kMaxL1 = 40;
+constexpr int kTabAD = 768;   // entries of the AD table (sum of 3 abs diffs, 0..765)
+constexpr int kTabCen = 96;   // entries of the census table (Hamming 0..64)
+constexpr int kTabAlpha = 64; // alpha*S by Lmin, 0..kMaxL1
+constexpr int kTabFloats = kTabAD + kTabCen + kTabAlpha;
+
+// Record rows are padded by kRPad records on both sides, so a candidate
+// x +- d with 0 <= d < 256 never leaves the allocation (its value is then
+// discarded: the cost of a match outside the image is 1).
+constexpr int kRPad = 256;
+
+// The H pass scans columns in warp segments of kHSeg, the V pass rows in
+// segments of 1 << seglog (powers of two: segment index = shift).
+constexpr int kHSegLog = 6, kHSeg = 1 << kHSegLog;
+constexpr int kHMaxLen = 1024;   // prefix columns one H block holds
+constexpr int kVMaxLen = 1024;   // prefix rows one V block holds
+
+struct PackArgs {
+    const uint8_t *rgb[2];
+    uint32_t *rgbx[2];
+    uint8_t *grey[2];
+    int npx;
+};
+
+struct PrepArgs {
+    const uint32_t *rgbx[2];
+    const uint8_t *grey[2];
+    uint4 *rec[2];         // first real record of row 0; row pitch rpitch
+    uchar4 *arms[2];
+    const float *tables;   // alpha*S table at offset kTabAD + kTabCen
+    int W, H, rpitch;
+    int cw, ch;            // census window (odd)
+    int L1, L2, tau1, tau2;
+};
+
+struct HArgs {
+    const uint4 *rec[2];   // padded rows, pitch rpitch
+    const uchar4 *arms[2];
+    uint32_t *sh[2];
+    const float *tables;
+    int W, H, D, rpitch;
+    int d0, dc;            // this pass covers d in [d0, d0 + dc)
+    int dstride;           // uint32 per pixel in sh (dc rounded up to 32)
+    int ngroups;           // 32-disparity groups in the pass
+    int L1;
+    int chunk;             // output columns per block
+    float S;               // fixed-point scale (integer valued)
+    uint32_t Sint;
+};
+
+struct VArgs {
+    const uint32_t *sh[2];
+    const uchar4 *arms[2];
+    unsigned long long *best[2];
+    int16_t *disp[2];
+    float *cost[2];
+    float *vol;            // optional (D, H, W) normalised costs of view `vol_view`
+    int vol_view;
+    int W, H, D;
+    int d0, dc, dstride;
+    int first, last;       // first / last pass of the d range
+    int L1;
+    int chunk;             // output rows per block
+    int seglog;            // rows per warp segment = 1 << seglog
+    float S;
+};
+
+} // namespace dco

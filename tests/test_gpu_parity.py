@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Every input is a seeded synthetic scene (paper_2203_02300_gb300.scenes).
+Tolerances: tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_02300_gb300 import scenes
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_02300_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    st = binding.Stereo(0)
+    yield torch, binding, st
+    st.close()
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def oparams(bp):
+    """oracle Params equal to a binding Params."""
+    return O.Params(lambda_ad=float(bp.lambda_ad), lambda_census=float(bp.lambda_census),
+                    gamma_l=float(bp.gamma_l), eps=float(bp.eps), census_w=bp.census_w,
+                    census_h=bp.census_h, arm_l1=bp.arm_l1, arm_l2=bp.arm_l2, tau1=bp.tau1,
+                    tau2=bp.tau2, lr_tol=bp.lr_tol)
+
+
+def run_views(env, left, right, D, bp=None):
+    torch, binding, st = env
+    out, dl, dr, cl, cr = st.match_views(dev(torch, left), dev(torch, right), D, bp)
+    torch.cuda.synchronize()
+    st.sync_status()
+    return (out.cpu().numpy(), dl.cpu().numpy(), dr.cpu().numpy(), cl.cpu().numpy(), cr.cpu().numpy())
+
+
+def full_check(env, left, right, D, bp=None, rows=None):
+    torch, binding, st = env
+    op = oparams(bp) if bp is not None else O.Params()
+    out, dl, dr, cl, cr = run_views(env, left, right, D, bp)
+    ref = O.match(left, right, D, op, rows=rows)
+    sl = slice(*rows) if rows else slice(None)
+    n = parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity")
+    n += parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity")
+    parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, "left cost")
+    parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, "right cost")
+    assert (out == O.lr_check(dl, dr, op.lr_tol)).all(), "consistency map"
+    return n, out, dl, dr
+
+
+# --------------------------------------------------------------- stages
+def stage_images():
+    s1 = scenes.config_scene(1)
+    s2 = scenes.config_scene(2)
+    rnd = [scenes.random_pair(w, h, 100 + w)[0] for (w, h) in ((1, 1), (7, 5), (33, 17), (130, 3))]
+    flat = np.full((20, 50, 3), 128, np.uint8)
+    return [s1.left, s1.right, s2.left] + rnd + [flat]
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_census_bit_exact(env, k):
+    torch, binding, st = env
+    img = stage_images()[k]
+    got = st.census(dev(torch, img)).cpu().numpy().view(np.uint64)
+    assert (got == O.census(img)).all()
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_arms_bit_exact(env, k):
+    torch, binding, st = env
+    img = stage_images()[k]
+    got = st.arms(dev(torch, img)).cpu().numpy()
+    assert (got == O.arms(img)).all()
+
+
+def test_census_and_arms_other_windows(env):
+    torch, binding, st = env
+    img = scenes.config_scene(1).left
+    for cw, ch, l1, l2, t1, t2 in ((7, 5, 10, 4, 15, 5), (11, 5, 40, 20, 30, 8), (1, 1, 1, 0, 256, 256)):
+        bp = binding.Params.default(census_w=cw, census_h=ch, arm_l1=l1, arm_l2=l2, tau1=t1, tau2=t2)
+        got = st.census(dev(torch, img), bp).cpu().numpy().view(np.uint64)
+        assert (got == O.census(img, cw, ch)).all()
+        got = st.arms(dev(torch, img), bp).cpu().numpy()
+        assert (got == O.arms(img, oparams(bp))).all()
+
+
+def test_lr_check_stage(env):
+    torch, binding, st = env
+    rng = np.random.default_rng(21)
+    dl = rng.integers(0, 9, (31, 45)).astype(np.int16)
+    dr = rng.integers(0, 9, (31, 45)).astype(np.int16)
+    for tol in (-1, 0, 1, 3):
+        got = st.lr_check(dev(torch, dl), dev(torch, dr), tol).cpu().numpy()
+        assert (got == O.lr_check(dl, dr, tol)).all()
+
+
+# ----------------------------------------------------------- full path
+def test_config1_full_parity(env):
+    s = scenes.config_scene(1)
+    n, out, dl, dr = full_check(env, s.left, s.right, s.D)
+    gt = np.rint(s.disp).astype(np.int16)
+    assert ((dl == gt) & ~s.occluded).sum() / (~s.occluded).sum() > 0.99
+
+
+def test_config2_full_parity(env):
+    s = scenes.config_scene(2)
+    full_check(env, s.left, s.right, s.D)
+
+
+def test_config1_cost_volume_both_views(env):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    ref = O.match(s.left, s.right, s.D, volume=True)
+    L, R = dev(torch, s.left), dev(torch, s.right)
+    for view, want in ((0, ref.vol_l), (1, ref.vol_r)):
+        got = st.cost_volume(L, R, s.D, view).cpu().numpy()
+        parity.check_volume(got, want, f"volume view {view}")
+
+
+@pytest.mark.parametrize("W,H,D", [(1, 1, 1), (7, 5, 3), (33, 17, 16), (100, 3, 40), (65, 40, 33),
+                                   (300, 40, 256), (64, 64, 64), (97, 71, 50)])
+def test_ragged_sizes(env, W, H, D):
+    s = scenes.plane_scene(W, H, D, 3, seed=1000 + W * H + D, drange=(0, max(0, min(D - 1, W - 1))),
+                           noise_sigma=1.0) if W >= 8 and H >= 8 else None
+    if s is None:
+        left, right = scenes.random_pair(W, H, 7 * W + H)
+    else:
+        left, right = s.left, s.right
+    full_check(env, left, right, D)
+
+
+@pytest.mark.parametrize("chunk", [1, 5, 16, 32, 33, 64])
+def test_passes_are_bit_identical(env, chunk):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    base = run_views(env, s.left, s.right, s.D)
+    got = run_views(env, s.left, s.right, s.D, binding.Params.default(d_chunk=chunk))
+    for a, b in zip(base, got):
+        assert np.array_equal(a, b)
+
+
+def test_identical_views(env):
+    rng = np.random.default_rng(31)
+    img = np.clip(np.rint(scenes._texture(rng, 60, 90)), 0, 255).astype(np.uint8)
+    out, dl, dr, cl, cr = run_views(env, img, img, 24)
+    assert (dl == 0).all() and (dr == 0).all() and (out == 0).all()
+    assert (cl == 0).all() and (cr == 0).all()
+
+
+@pytest.mark.parametrize("over", [dict(lr_tol=-1), dict(lr_tol=0), dict(arm_l1=5, arm_l2=2),
+                                  dict(gamma_l=3.0, eps=0.5), dict(lambda_ad=30.0, lambda_census=15.0),
+                                  dict(census_w=7, census_h=5), dict(arm_l1=40, arm_l2=40, tau1=256, tau2=256)])
+def test_parameter_variants(env, over):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    full_check(env, s.left, s.right, s.D, binding.Params.default(**over))
+
+
+def test_config5_sampled_rows(env):
+    # 1920x1080 D=256 at the benchmark's launch configuration; the oracle
+    # evaluates three row bands (top border, middle, bottom border)
+    s = scenes.config_scene(5)
+    torch, binding, st = env
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
+    for rows in ((0, 6), (537, 543), (1074, 1080)):
+        ref = O.match(s.left, s.right, s.D, rows=rows)
+        sl = slice(*rows)
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r)
+        parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
+        parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
+    assert (out == O.lr_check(dl, dr, 1)).all()
+
+
+def test_match_host_equals_device_path(env):
+    torch, binding, st = env
+    s = scenes.config_scene(2)
+    out = st.match(dev(torch, s.left), dev(torch, s.right), s.D).cpu().numpy()
+    host = st.match_host(s.left, s.right, s.D)
+    assert np.array_equal(out, host)
+
+
+def test_repeat_runs_bit_identical(env):
+    s = scenes.config_scene(2)
+    a = run_views(env, s.left, s.right, s.D)
+    b = run_views(env, s.left, s.right, s.D)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+# ----------------------------------------------------------- errors
+def test_argument_errors(env):
+    torch, binding, st = env
+    L = dev(torch, np.zeros((8, 8, 3), np.uint8))
+    out = torch.empty((8, 8), dtype=torch.int16, device="cuda")
+    lib = binding.lib()
+    h = st._h
+    s0 = torch.cuda.current_stream().cuda_stream
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 9, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 0, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 0, 8, 1, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, None, L.data_ptr(), 8, 8, 4, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 4, None, None, s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(None, L.data_ptr(), L.data_ptr(), 8, 8, 4, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    for bad in (dict(census_w=8), dict(census_w=13, census_h=7), dict(arm_l1=41), dict(arm_l1=0),
+                dict(lambda_ad=0.0), dict(eps=-1.0), dict(d_chunk=-1)):
+        p = binding.Params.default(**bad)
+        import ctypes
+        assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 4, ctypes.byref(p), out.data_ptr(),
+                                    s0) == binding.DCO_EINVAL, bad
+    st.sync_status()
+
+
+def test_budget_rejects_before_launch(env):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    small = binding.Stereo(0, budget_bytes=1 << 20)
+    with pytest.raises(binding.DcoError) as e:
+        small.match(dev(torch, s.left), dev(torch, s.right), s.D)
+    assert e.value.code == binding.DCO_EBUDGET
+    # a budget that fits per-pixel buffers plus one 32-disparity pass works
+    need = binding.Stereo.workspace_bytes(s.W, s.H, s.D, binding.Params.default(d_chunk=32))
+    mid = binding.Stereo(0, budget_bytes=need)
+    out = mid.match(dev(torch, s.left), dev(torch, s.right), s.D).cpu().numpy()
+    ref = st.match(dev(torch, s.left), dev(torch, s.right), s.D).cpu().numpy()
+    assert np.array_equal(out, ref)
+    small.close()
+    mid.close()
