@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the AD-census matcher (arXiv 2203.02300, Sect. 4) on GB300.
+
+Workload: one rectified RGB pair, 640x480, D = 64 (seeded synthetic scene of
+12 slanted planes, Gaussian noise sigma 2, right view gain 1.03 offset +5).
+A step is one pass of the whole path on that pair: grey/census/arms for both
+views, Eq. 1 costs, Eq. 2 aggregation, Eq. 3 WTA for both reference views,
+left-right check.  Metric: disparity evaluations per second, W*H*D per pair.
+
+Own arm (default): inputs resident in HBM; the L2 (129 MB) is flushed by a
+256 MiB write between timed steps (outside the step's CUDA events); steps are
+timed with CUDA events on the launching stream.  Under torchrun each rank
+runs an independent replica on its own GPU (no collective on the data path);
+the total is divided by the slowest rank's time.
+
+--impl reference: the FP64 CPU oracle, on the host cores, on bounded row
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W, H, D = 640, 480, 64
+CONFIG = {"workload": "single rectified RGB pair 640x480 D=64, 12 slanted planes, noise sigma 2, "
+                      "right gain 1.03 offset +5 (seeded synthetic)",
+          "W": W, "H": H, "D": D, "views": 2, "lr_check": True,
+          "l2": "flushed between timed steps by a 256 MiB write outside the step events"}
+METRIC = "disparity evals/sec (W*H*D per pair per second) at 640x480 D=64"
+UNIT = "evals/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return PEAKS_FALLBACK, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2203_02300_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    that summary was taken on the current kernel source (else None)."""
+    dig = source_digest()
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md")):
+        text = open(path).read()
+        m = re.search(r"source_digest:\s*(\w+)", text)
+        t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if m and t and m.group(1) == dig:
+            return float(t.group(1))
+    return None
+
+
+# ------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except OSError:
+            rows = []
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            res = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return res
+
+
+# --------------------------------------------------------------- own arm
+# Algorithmic HBM bytes of each kernel per launch (what the method must move:
+# inputs read once, outputs written once).  npx = W*H, ev = view-evaluations
+# of the pass (2 views * npx * disparities of the pass).
+def algorithmic_bytes(kernel: str, npx: int, ev_pass: int, npass: int) -> float:
+    if kernel == "k_pack":
+        return 2 * npx * (3 + 4 + 1)                       # rgb in, rgbx + grey out
+    if kernel == "k_prep":
+        return 2 * npx * (4 + 1 + 16 + 4)                  # rgbx + grey in, record + arms out
+    if kernel == "k_hagg":
+        return 4 * ev_pass + 2 * npx * (16 + 16 + 4)       # slice out; records + arms in
+    if kernel == "k_vagg":
+        return 4 * ev_pass + 2 * npx * (4 + 2 + (16 if npass > 1 else 0))   # slice in; arms in, disparity/state out
+    if kernel == "k_lr":
+        return npx * (2 + 2 + 2)
+    return 0.0
+
+
+def own_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    from paper_2203_02300_gb300 import binding, scenes, tune
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device(f"cuda:{local_rank}")
+    s = scenes.config_scene(2)
+    Lh = torch.from_numpy(s.left).pin_memory()
+    Rh = torch.from_numpy(s.right).pin_memory()
+    L = Lh.to(dev)
+    R = Rh.to(dev)
+    out = torch.empty((H, W), dtype=torch.int16, device=dev)
+    st = binding.Stereo(local_rank)
+    dchunk = 0 if args.no_tune else tune.tune_d_chunk(st, L, R, D)
+    p = binding.Params.default(d_chunk=dchunk)
+    npass = -(-D // (dchunk or D))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        st.match(L, R, D, p, out)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, L2 flushed between steps
+    clocks = Clocks(local_rank if torch.cuda.device_count() > 1 else 0)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = st.launch_count()
+    t_wall0 = time.perf_counter()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        st.match(L, R, D, p, out)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    launches = st.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = W * H * D * args.steps * world
+    value = units / (total_ms * 1e-3)
+
+    # ---- end to end: host buffers through the C ABI (copies inside)
+    Ln, Rn = Lh.numpy(), Rh.numpy()
+    outh = torch.empty((H, W), dtype=torch.int16).pin_memory().numpy()
+    for _ in range(3):
+        st.match_host(Ln, Rn, D, p, out=outh)
+    e2e_ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st.match_host(Ln, Rn, D, p, out=outh)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = units / (e2e_total * 1e-3)
+    check = st.match(L, R, D, p, out)
+    torch.cuda.synchronize(dev)
+    assert np.array_equal(outh, check.cpu().numpy()), "host path differs from device path"
+
+    # ---- per-kernel durations (library CUDA events on the same stream)
+    st.set_profiling(True)
+    st.profile_reset()
+    for _ in range(args.steps):
+        flush.zero_()
+        st.match(L, R, D, p, out)
+    torch.cuda.synchronize(dev)
+    prof = st.profile()
+    st.set_profiling(False)
+    npx = W * H
+    dc = dchunk or D
+    kernels = {}
+    for k, (n, ms) in prof.items():
+        avg = ms / n
+        ev_pass = 2 * npx * dc
+        kernels[k] = {"launches": n, "avg_us": round(avg * 1e3, 3),
+                      "share": None, "alg_bytes": algorithmic_bytes(k, npx, ev_pass, npass)}
+    ktot = sum(v["avg_us"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = round(v["avg_us"] * v["launches"] / ktot, 4)
+    dom = max(kernels, key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
+    pk, src = peaks()
+    achieved = kernels[dom]["alg_bytes"] / (kernels[dom]["avg_us"] * 1e-6) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+            "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
+            if src == "measured" else "fallback 6.8 TB/s"}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(s, budget_s=12.0)
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 cost, u32 fixed-point aggregation",
+            "data": "synthetic (seeded plane scene; the paper's INDEMIND / Middlebury data are not available)",
+            "config": dict(CONFIG, d_chunk=dc, passes=npass, parallelism=f"replicas x{world}"),
+            "frames_per_s": 1e3 * args.steps * world / total_ms,
+            "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 3,
+                    "d2h_bytes_per_step": W * H * 2,
+                    "latency_ms": {"p50": statistics.median(e2e_ms),
+                                   "p99": sorted(e2e_ms)[min(len(e2e_ms) - 1, int(0.99 * len(e2e_ms)))]}},
+            "roofline": roof,
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]},
+            "wall_s_timed_region": t_wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- oracle timing
+def oracle_rate(scene, budget_s: float, rows_per_sample: int = 0):
+    """The FP64 oracle as it stands, on all host cores, on row bands of the
+    workload until about budget_s of CPU work; evals/s in the metric's unit."""
+    from oracle import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    rows = rows_per_sample or H
+    done_units, t_used, y0, n = 0, 0.0, 0, 0
+    while t_used < budget_s and n < 64:
+        y1 = min(H, y0 + rows)
+        t0 = time.perf_counter()
+        O.match(scene.left, scene.right, D, rows=(y0, y1))
+        t_used += time.perf_counter() - t0
+        done_units += W * (y1 - y0) * D
+        y0 = 0 if y1 >= H else y1
+        n += 1
+    return {"value": done_units / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle runs of {rows} rows x 640 cols x D=64 (both views + LR), "
+                      f"{t_used:.1f} s of host time, FP64 C with OpenMP over rows"}
+
+
+def reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    from oracle import oracle as O
+    from paper_2203_02300_gb300 import scenes
+    obuild.build()
+    s = scenes.config_scene(2)
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    rows = 32   # a bounded band per step keeps K + W steps within minutes
+    band = lambda k: ((k * rows) % H, min(H, (k * rows) % H + rows))
+    for k in range(args.warmup):
+        O.match(s.left, s.right, D, rows=band(k))
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        O.match(s.left, s.right, D, rows=band(k))
+        times.append(time.perf_counter() - t0)
+    units = W * rows * D * args.steps
+    value = units / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded plane scene)",
+            "config": dict(CONFIG, sample_rows_per_step=rows),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows}-row band of the 640x480 D=64 pair per step (both views + LR)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        own_arm(args)
+
+
+if __name__ == "__main__":
+    main()

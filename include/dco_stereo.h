@@ -222,6 +222,9 @@ const char *dco_stereo_last_error(dco_stereo *h);
  * and their summed duration in milliseconds.
  */
 dco_status dco_stereo_set_profiling(dco_stereo *h, int enable);
+
+/* Number of kernels the handle has launched since it was created. */
+unsigned long long dco_stereo_launch_count(dco_stereo *h);
 dco_status dco_stereo_profile_reset(dco_stereo *h);
 int dco_stereo_profile_count(dco_stereo *h);
 dco_status dco_stereo_profile_get(dco_stereo *h, int i, const char **name, int *launches,

@@ -91,6 +91,7 @@ def lib():
             "dco_stereo_profile_reset": (c_int, [P]),
             "dco_stereo_profile_count": (c_int, [P]),
             "dco_stereo_profile_get": (c_int, [P, c_int, P, P, P]),
+            "dco_stereo_launch_count": (ctypes.c_ulonglong, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -257,6 +258,9 @@ class Stereo:
 
     def profile_reset(self) -> None:
         _check(lib().dco_stereo_profile_reset(self._h), self._h)
+
+    def launch_count(self) -> int:
+        return int(lib().dco_stereo_launch_count(self._h))
 
     def profile(self) -> dict:
         """{kernel name: (launches, total ms)} since the last reset."""

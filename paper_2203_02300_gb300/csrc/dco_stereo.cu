@@ -556,6 +556,7 @@ struct dco_stereo {
     uint8_t *stage = nullptr;
     size_t stage_cap = 0;
     bool profiling = false;
+    unsigned long long launches = 0;
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> pool;
     std::vector<ProfAgg> agg;
@@ -615,6 +616,7 @@ struct ProfScope {
     ProfEvent ev{};
     ProfScope(dco_stereo *h_, cudaStream_t s_, const char *name) : h(h_), s(s_)
     {
+        h->launches++;
         if (h->profiling) {
             ev.name = name;
             ev.a = take_event(h);
@@ -976,6 +978,7 @@ dco_status dco_stereo_census(dco_stereo *h, const uint8_t *rgb, int W, int H, co
     if ((st = launch_prep(h, p, dv, L, rgb, rgb, 1, nullptr, W, H, s)) != DCO_OK)
         return st;
     const size_t n = (size_t)W * H;
+    ProfScope ps(h, s, "k_extract_census");
     k_extract_census<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec_ptr(h, L.rec[0]), W, H, L.rpitch,
                                                                   reinterpret_cast<unsigned long long *>(census_out));
     DCO_CUDA(h, cudaGetLastError());
@@ -1087,6 +1090,11 @@ dco_status dco_stereo_profile_get(dco_stereo *h, int i, const char **name, int *
     if (launches) *launches = h->agg[i].launches;
     if (total_ms) *total_ms = h->agg[i].ms;
     return DCO_OK;
+}
+
+unsigned long long dco_stereo_launch_count(dco_stereo *h)
+{
+    return h ? h->launches : 0ull;
 }
 
 const char *dco_stereo_last_error(dco_stereo *h)
