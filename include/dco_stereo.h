@@ -211,6 +211,30 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
  */
 dco_status dco_stereo_sync_status(dco_stereo *h);
 
+/*
+ * The whole path of dco_stereo_match for callers that cannot allocate
+ * device memory (for example code running where cudaMalloc is forbidden
+ * or unavailable, or a host that must keep its memory footprint fixed after
+ * start-up).  It takes no handle and allocates nothing: its workspace and
+ * tables live in one 32 MiB device array built into the library, which
+ * every GPU that loads the library holds until the process exits.  The
+ * paper has no counterpart; this is an integration entry point.
+ *   - Runs on the calling thread's current CUDA device.  The first call on a
+ *     device looks up the array's device address; make that first call
+ *     before any stream capture.
+ *   - Sizes whose workspace (passes of 32 disparities) does not fit the
+ *     array return DCO_EBUDGET before anything is enqueued: roughly
+ *     W*H <= 90 000 pixels (e.g. 320x240) at any D <= 256.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     nothing in it needs to start at zero (every word a kernel reads was
+ *     written earlier in the same call).  Calls that overlap on the GPU
+ *     (other streams, other threads) race on it: serialise them.
+ * left, right: device W*H*3 bytes; disp_out: device W*H int16; p = NULL
+ * uses the defaults (p->d_chunk is ignored).
+ */
+dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_t *right, int W, int H, int D,
+                                    const dco_params *p, int16_t *disp_out, dco_stream stream);
+
 /* Text of the last CUDA or budget error seen by the handle ("" if none).
  * Owned by the handle, valid until its next call. */
 const char *dco_stereo_last_error(dco_stereo *h);

@@ -92,6 +92,7 @@ def lib():
             "dco_stereo_profile_count": (c_int, [P]),
             "dco_stereo_profile_get": (c_int, [P, c_int, P, P, P]),
             "dco_stereo_launch_count": (ctypes.c_ulonglong, [P]),
+            "dco_stereo_match_noalloc": (c_int, [P, P, c_int, c_int, c_int, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

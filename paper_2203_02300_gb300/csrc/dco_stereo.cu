@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1103,3 +1104,83 @@ const char *dco_stereo_last_error(dco_stereo *h)
 }
 
 } // extern "C"
+
+// ======================================================= no-allocation entry
+// For callers that may not allocate device memory: the scratch lives in one
+// file-scope device array that every GPU loading this library holds until
+// exit.  Host code never uses the array's name as a device address: each
+// device's address comes from cudaGetSymbolAddress, taken once per device
+// on the first call with that device current.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[kNoAllocMaxDevices] = {};
+} // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+dco_status noalloc_base(int dev, void **out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return DCO_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DCO_ECUDA;
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return DCO_OK;
+}
+} // namespace
+
+extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_t *right, int W, int H, int D,
+                                               const dco_params *pin, int16_t *disp_out, dco_stream stream)
+{
+    dco_params p;
+    if (pin) p = *pin;
+    else dco_params_default(&p);
+    if (!params_valid(p) || !left || !right || !disp_out || !dims_valid(W, H, D)) return DCO_EINVAL;
+    p.d_chunk = 32;   // passes of 32 disparities keep the slices small
+    Derived dv;
+    derive(p, dv);
+    const size_t tab_bytes = align_up(sizeof(float) * kTabFloats);
+    const Layout L = make_layout(W, H, D, p);
+    if (tab_bytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DCO_ECUDA;
+    void *base = nullptr;
+    dco_status st = noalloc_base(dev, &base);
+    if (st != DCO_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // Eq. 1 tables (host double, rounded once to float) into the scratch
+    float tab[kTabFloats];
+    for (int k = 0; k < kTabAD; k++)
+        tab[k] = k <= 765 ? (float)(1.0 - std::exp(-(k / 3.0) / (double)p.lambda_ad)) : 1.0f;
+    for (int k = 0; k < kTabCen; k++)
+        tab[kTabAD + k] = k <= 64 ? (float)(1.0 - std::exp(-(double)k / (double)p.lambda_census)) : 1.0f;
+    for (int l = 0; l < kTabAlpha; l++) {
+        const double alpha = 1.0 - std::exp(-(double)p.gamma_l / ((double)l + (double)p.eps));
+        tab[kTabAD + kTabCen + l] = (float)(alpha * (double)dv.Sint);
+    }
+    if (cudaMemcpyAsync(base, tab, sizeof tab, cudaMemcpyHostToDevice, s) != cudaSuccess) return DCO_ECUDA;
+
+    // a handle that owns nothing: its workspace and tables are the scratch
+    dco_stereo view;
+    view.device = dev;
+    view.ws = static_cast<char *>(base) + tab_bytes;
+    view.ws_cap = kNoAllocScratchBytes - tab_bytes;
+    view.d_tables = static_cast<float *>(base);
+    view.tab_valid = true;
+    view.tab_key[0] = p.lambda_ad;
+    view.tab_key[1] = p.lambda_census;
+    view.tab_key[2] = p.gamma_l;
+    view.tab_key[3] = p.eps;
+    view.tab_l1 = p.arm_l1;
+    st = run_match(&view, left, right, W, H, D, p, disp_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s);
+    view.ws = nullptr;
+    view.d_tables = nullptr;
+    return st;
+}
