@@ -34,38 +34,75 @@
 
 namespace dco {
 
-// ------------------------------------------------------------------ helpers
-__device__ __forceinline__ int maxdiff3(uint32_t a, uint32_t b)
-{
-    const uint32_t d = __vabsdiffu4(a, b);
-    return max(max(int(d & 0xffu), int((d >> 8) & 0xffu)), int((d >> 16) & 0xffu));
-}
-
 // ------------------------------------------------------------------ k_pack
 // RGB (3 bytes per pixel) -> packed 32-bit colour and the integer grey level
-// of the census, for both images.
+// of the census, for both images; four pixels (12 bytes) per thread.
+__device__ __forceinline__ uint32_t grey_of(uint32_t c)
+{
+    return (77u * (c & 0xffu) + 150u * ((c >> 8) & 0xffu) + 29u * ((c >> 16) & 0xffu) + 128u) >> 8;
+}
+
 __global__ void k_pack(PackArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.npx) return;
-    const uint8_t *p = (blockIdx.y ? a.rgb[1] : a.rgb[0]) + 3 * (size_t)i;
-    const uint32_t r = __ldg(p), g = __ldg(p + 1), b = __ldg(p + 2);
-    (blockIdx.y ? a.rgbx[1] : a.rgbx[0])[i] = r | (g << 8) | (b << 16);
-    (blockIdx.y ? a.grey[1] : a.grey[0])[i] = (uint8_t)((77 * r + 150 * g + 29 * b + 128) >> 8);
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;   // pixels 4q .. 4q+3
+    const int i0 = 4 * q;
+    if (i0 >= a.npx) return;
+    const uint8_t *rgb = blockIdx.y ? a.rgb[1] : a.rgb[0];
+    uint32_t *rgbx = blockIdx.y ? a.rgbx[1] : a.rgbx[0];
+    uint8_t *grey = blockIdx.y ? a.grey[1] : a.grey[0];
+    uint32_t c[4];
+    if (i0 + 4 <= a.npx && ((reinterpret_cast<uintptr_t>(rgb) & 3u) == 0)) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * (size_t)i0);
+        const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+        c[0] = w0 & 0x00ffffffu;
+        c[1] = __funnelshift_r(w0, w1, 24) & 0x00ffffffu;
+        c[2] = __funnelshift_r(w1, w2, 16) & 0x00ffffffu;
+        c[3] = w2 >> 8;
+    } else {
+        for (int k = 0; k < 4; k++) {
+            const int i = min(i0 + k, a.npx - 1);
+            const uint8_t *p = rgb + 3 * (size_t)i;
+            c[k] = uint32_t(__ldg(p)) | (uint32_t(__ldg(p + 1)) << 8) | (uint32_t(__ldg(p + 2)) << 16);
+        }
+    }
+    if (i0 + 4 <= a.npx) {
+        *reinterpret_cast<uint4 *>(rgbx + i0) = make_uint4(c[0], c[1], c[2], c[3]);
+        *reinterpret_cast<uint32_t *>(grey + i0) =
+            grey_of(c[0]) | (grey_of(c[1]) << 8) | (grey_of(c[2]) << 16) | (grey_of(c[3]) << 24);
+    } else {
+        for (int k = 0; i0 + k < a.npx; k++) {
+            rgbx[i0 + k] = c[k];
+            grey[i0 + k] = (uint8_t)grey_of(c[k]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ k_prep
 // One thread per pixel of a 32 x 8 tile.  Census (Sect. 4.2.1) from the grey
 // tile with its window halo in shared memory (clamp-to-edge on load); the
 // four arms (Sect. 4.1) by walking the packed colours through L1 (arms are
-// short on textured input, so no L1-wide halo is staged).
+// short on textured input, so no L1-wide halo is staged).  The 9x7 census
+// compares four neighbours per SIMD byte comparison.
 constexpr int kTX = 32, kTY = 8;
 constexpr int kMaxCW = 15, kMaxCH = 15;
+constexpr int kGW = 48;   // grey tile row pitch (>= kTX + kMaxCW - 1, multiple of 4)
+
+// any colour channel of |a - b| >= t, t4 = t replicated in four bytes (t <= 255)
+__device__ __forceinline__ bool any_ge(uint32_t a, uint32_t b, uint32_t t4)
+{
+    return (__vcmpgeu4(__vabsdiffu4(a, b), t4) & 0x00ffffffu) != 0u;
+}
+
+// 4 flags f_i = [byte_i(w) < c] -> bits f0 | f1<<1 | f2<<2 | f3<<3
+__device__ __forceinline__ uint32_t lt4(uint32_t w, uint32_t c4)
+{
+    return (__vsetltu4(w, c4) * 0x01020408u) >> 24;
+}
 
 template <int CW, int CH>
 __global__ void __launch_bounds__(kTX * kTY) k_prep(PrepArgs a)
 {
-    __shared__ uint8_t gs[kTY + kMaxCH - 1][kTX + kMaxCW - 1];
+    __shared__ __align__(16) uint8_t gs[kTY + kMaxCH - 1][kGW];
     const int img = blockIdx.z;
     const uint32_t *__restrict__ rgbx = img ? a.rgbx[1] : a.rgbx[0];
     const uint8_t *__restrict__ grey = img ? a.grey[1] : a.grey[0];
@@ -86,40 +123,92 @@ __global__ void __launch_bounds__(kTX * kTY) k_prep(PrepArgs a)
     if (x >= W || y >= H) return;
 
     // census: bit k = [Y(n) < Y(p)], window row-major, centre skipped
-    const int yc = gs[ty + ry][tx + rx];
-    uint32_t lo = 0, hi = 0;
-    int k = 0;
+    const uint32_t yc = gs[ty + ry][tx + rx];
+    unsigned long long bits = 0ull;
+    if (CW == 9 && CH == 7) {
+        const uint32_t c4 = yc * 0x01010101u;
+        const int al = tx & ~3, sh = 8 * (tx & 3);
+        int k = 0;
 #pragma unroll
-    for (int dy = 0; dy < (CH ? CH : kMaxCH); dy++) {
-        if (!CH && dy >= ch) break;
-#pragma unroll
-        for (int dx = 0; dx < (CW ? CW : kMaxCW); dx++) {
-            if (!CW && dx >= cw) break;
-            if (dy == ry && dx == rx) continue;
-            const uint32_t bit = gs[ty + dy][tx + dx] < yc ? 1u : 0u;
-            if (k < 32) lo |= bit << k; else hi |= bit << (k - 32);
-            k++;
+        for (int dy = 0; dy < 7; dy++) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(&gs[ty + dy][al]);
+            const uint32_t a0 = row[0], a1 = row[1], a2 = row[2];
+            const uint32_t w0 = __funnelshift_r(a0, a1, sh);   // bytes dx 0..3
+            const uint32_t w1 = __funnelshift_r(a1, a2, sh);   // bytes dx 4..7
+            const uint32_t b8 = (__funnelshift_r(a2, 0u, sh) & 0xffu) < yc ? 1u : 0u;   // dx 8
+            const uint32_t f0 = lt4(w0, c4), f1 = lt4(w1, c4);
+            uint32_t rowbits;
+            int nb;
+            if (dy == 3) {   // centre row: dx 4 is the centre itself
+                rowbits = f0 | ((f1 >> 1) << 4) | (b8 << 7);
+                nb = 8;
+            } else {
+                rowbits = f0 | (f1 << 4) | (b8 << 8);
+                nb = 9;
+            }
+            bits |= (unsigned long long)rowbits << k;
+            k += nb;
+        }
+    } else {
+        int k = 0;
+        for (int dy = 0; dy < ch; dy++) {
+            for (int dx = 0; dx < cw; dx++) {
+                if (dy == ry && dx == rx) continue;
+                if (gs[ty + dy][tx + dx] < yc) bits |= 1ull << k;
+                k++;
+            }
         }
     }
 
     // arms: largest k <= L1 whose steps all pass the double threshold
     const size_t i = (size_t)y * W + x;
     const uint32_t p = __ldg(rgbx + i);
-    const int L1 = a.L1, L2 = a.L2, tau1 = a.tau1, tau2 = a.tau2;
+    const int L1 = a.L1, L2 = a.L2;
+    // a threshold >= 256 never stops an arm (channel differences are <= 255)
+    const bool use1 = a.tau1 < 256, use2 = a.tau2 < 256;
+    const uint32_t t1 = 0x01010101u * (uint32_t)min(a.tau1, 255);
+    const uint32_t t2 = 0x01010101u * (uint32_t)min(a.tau2, 255);
+    // the first kArmBatch candidates of all four directions are loaded at
+    // once (in-image addresses only), so a typical pixel pays one load latency
+    constexpr int kArmBatch = 2;
     int arm[4];
+    uint32_t cand[4][kArmBatch];
+    int lim[4];
+    ptrdiff_t step[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
         const int room = e == 0 ? x : (e == 1 ? W - 1 - x : (e == 2 ? y : H - 1 - y));
-        const ptrdiff_t step = e == 0 ? -1 : (e == 1 ? 1 : (e == 2 ? -(ptrdiff_t)W : (ptrdiff_t)W));
-        const int lim = min(L1, room);
-        const uint32_t *q = rgbx + i;
+        step[e] = e == 0 ? -1 : (e == 1 ? 1 : (e == 2 ? -(ptrdiff_t)W : (ptrdiff_t)W));
+        lim[e] = min(L1, room);
+#pragma unroll
+        for (int u = 0; u < kArmBatch; u++)
+            cand[e][u] = u < lim[e] ? __ldg(rgbx + i + (u + 1) * step[e]) : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
         uint32_t prev = p;
         int n = 0;
-        for (int j = 1; j <= lim; j++) {
-            q += step;
-            const uint32_t c = __ldg(q);
-            const int dp = maxdiff3(c, p);
-            if (dp >= tau1 || maxdiff3(c, prev) >= tau1 || (j > L2 && dp >= tau2)) break;
+        bool open = true;
+#pragma unroll
+        for (int u = 0; u < kArmBatch; u++) {
+            const int j = u + 1;
+            if (open && j <= lim[e]) {
+                const uint32_t c = cand[e][u];
+                if ((use1 && (any_ge(c, p, t1) || any_ge(c, prev, t1))) || (j > L2 && use2 && any_ge(c, p, t2)))
+                    open = false;
+                else {
+                    n = j;
+                    prev = c;
+                }
+            } else {
+                open = false;
+            }
+        }
+        // rare long arms: continue one candidate at a time
+        for (int j = kArmBatch + 1; open && j <= lim[e]; j++) {
+            const uint32_t c = __ldg(rgbx + i + j * step[e]);
+            if ((use1 && (any_ge(c, p, t1) || any_ge(c, prev, t1))) || (j > L2 && use2 && any_ge(c, p, t2)))
+                break;
             n = j;
             prev = c;
         }
@@ -128,7 +217,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_prep(PrepArgs a)
     const int lmin = min(min(arm[0], arm[1]), min(arm[2], arm[3]));
     const float alphaS = __ldg(a.tables + kTabAD + kTabCen + lmin);
     (img ? a.rec[1] : a.rec[0])[(size_t)y * a.rpitch + x] =
-        make_uint4(lo, hi, p | (uint32_t(lmin) << 24), __float_as_uint(alphaS));
+        make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), p | (uint32_t(lmin) << 24), __float_as_uint(alphaS));
     (img ? a.arms[1] : a.arms[0])[i] = make_uchar4((uint8_t)arm[0], (uint8_t)arm[1], (uint8_t)arm[2], (uint8_t)arm[3]);
 }
 
@@ -213,66 +302,100 @@ __global__ void __launch_bounds__(16 * 32) k_hagg(HArgs a)
     const int d = dlo + lane;
     const bool live = d <= dhi;
     const int oi = (live ? sign * d : sign * dlo) - olo;   // candidate index = x + oi (in range)
+    // columns x (relative to xa) whose match x -/+ d lies in the image
+    const int vlo = live ? (view ? 0 : max(0, d - xa)) : 1, vhi = live ? (view ? W - d - xa : len) : 0;
     const float Sf = a.S;
     const uint32_t Sint = a.Sint;
 
     // ---- A: costs and local prefix of this warp's segment
     const int sa = warp * kHSeg, sb = min(len, sa + kHSeg);   // relative to xa
     uint32_t run = 0;
-    for (int x0 = sa; x0 < sb; x0 += kHU) {
+    auto cost_at = [&](const uint4 pr, const uint4 po, int x) -> uint32_t {
+        const int h = __popc(pr.x ^ po.x) + __popc(pr.y ^ po.y);
+        const int k = (int)__dp4a(__vabsdiffu4(pr.z, po.z), 0x00010101u, 0u);
+        const float av = __uint_as_float(pr.w);
+        const uint32_t q = __float2uint_rn(fmaf(av, sTA[k], (Sf - av) * sTC[h]));
+        return (unsigned)(x - vlo) < (unsigned)(vhi - vlo) ? q : Sint;   // match outside the image: cost 1
+    };
+    int x0 = sa;
+    for (; x0 + kHU <= sb; x0 += kHU) {
         uint4 pr[kHU], po[kHU];
 #pragma unroll
         for (int u = 0; u < kHU; u++) {
-            const int x = min(x0 + u, sb - 1);
-            pr[u] = sref[x];
-            po[u] = soth[x + xa + oi];
+            pr[u] = sref[x0 + u];
+            po[u] = soth[x0 + u + xa + oi];
         }
+        uint32_t c[kHU];
+#pragma unroll
+        for (int u = 0; u < kHU; u++) c[u] = cost_at(pr[u], po[u], x0 + u);
 #pragma unroll
         for (int u = 0; u < kHU; u++) {
-            const int h = __popc(pr[u].x ^ po[u].x) + __popc(pr[u].y ^ po[u].y);
-            const int k = (int)__dp4a(__vabsdiffu4(pr[u].z, po[u].z), 0x00010101u, 0u);
-            const float av = __uint_as_float(pr[u].w);
-            const uint32_t q = __float2uint_rn(fmaf(av, sTA[k], (Sf - av) * sTC[h]));
-            const bool in = live && (unsigned)(xa + x0 + u + sign * d) < (unsigned)W;
-            if (x0 + u < sb) {
-                run += in ? q : Sint;   // match outside the image: cost 1
-                P[(x0 + u) * 32 + lane] = run;
-            }
+            run += c[u];
+            P[(x0 + u) * 32 + lane] = run;
         }
+    }
+    for (; x0 < sb; x0++) {
+        run += cost_at(sref[x0], soth[x0 + xa + oi], x0);
+        P[x0 * 32 + lane] = run;
     }
     T[warp * 32 + lane] = run;
     __syncthreads();
     // ---- B: exclusive segment offsets, added in place
     uint32_t offs = 0;
     for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
-    if (warp > 0)
-        for (int x = sa; x < sb; x++) P[x * 32 + lane] += offs;
+    if (warp > 0) {
+        uint32_t *q = P + sa * 32 + lane;
+        int x = sa;
+        for (; x + 8 <= sb; x += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) q[u * 32] += offs;
+            q += 256;
+        }
+        for (; x < sb; x++, q += 32) *q += offs;
+    }
     __syncthreads();
     // ---- C: horizontal segment sums of the output columns
-    uint32_t *out = (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32 + lane;
     const int n_out = xe - xs, base = xs - xa;
-    for (int i = warp; i < n_out; i += nw) {
+    const size_t ostep = (size_t)nw * a.dstride;
+    uint32_t *o = (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs + warp) * a.dstride + g * 32 + lane;
+    const uint32_t *Pl = P + lane;
+    int i = warp;
+    for (; i + nw < n_out; i += 2 * nw, o += 2 * ostep) {
+        const uchar4 am0 = sarm[i], am1 = sarm[i + nw];
+        const int hi0 = base + i + am0.y, lo0 = base + i - am0.x - 1;   // lo >= -1
+        const int hi1 = base + i + nw + am1.y, lo1 = base + i + nw - am1.x - 1;
+        const uint32_t v0 = Pl[hi0 * 32] - (lo0 >= 0 ? Pl[lo0 * 32] : 0u);
+        const uint32_t v1 = Pl[hi1 * 32] - (lo1 >= 0 ? Pl[lo1 * 32] : 0u);
+        o[0] = v0;
+        o[ostep] = v1;
+    }
+    if (i < n_out) {
         const uchar4 am = sarm[i];
-        const int hi = base + i + am.y, lo = base + i - am.x - 1;   // lo >= -1
-        const uint32_t plo = lo >= 0 ? P[lo * 32 + lane] : 0u;
-        out[(size_t)i * a.dstride] = P[hi * 32 + lane] - plo;
+        const int hi = base + i + am.y, lo = base + i - am.x - 1;
+        *o = Pl[hi * 32] - (lo >= 0 ? Pl[lo * 32] : 0u);
     }
 }
 
 // ------------------------------------------------------------------ k_vagg
 // Block = one column x of one reference view, a chunk of output rows.  The
-// prefix range [ya, yb) is split into warp segments of 1 << seglog rows.
-// For each group of 32 disparities of the pass (lane = disparity):
-//   A. each warp copies (cp.async) its segment of the S_H column into
-//      Q[y - ya][lane] and turns it into a local prefix in place (and, once,
-//      the arm words and the prefix of the segment lengths l + r + 1);
-//   B. exclusive segment offsets, added in place;
-//   C. each row yo: V = Q(yo + dn) - Q(yo - up - 1) (Eq. 2, the sum over the
-//      vertical arm of the horizontal sums; N does not depend on d, so the
-//      WTA compares V) -> warp min-reduction (Eq. 3, smallest d on ties)
-//      merged into the block's running best of the row.
+// prefix range [ya, yb) is split into warp segments of 32 rows.  For each
+// group of 32 disparities of the pass:
+//   A. lane = disparity: each warp loads its 32 slice rows into registers
+//      (one 128-byte line per row), sums them, exchanges the segment sums
+//      with the other warps, and writes the column prefix (with its segment
+//      offset) to Q[y - ya][lane] (row stride 33 words): one shared store per
+//      evaluation;
+//   C. lane = output row: V(d) = Q(y + dn, d) - Q(y - up - 1, d) for the 32
+//      disparities (Eq. 2: the sum over the vertical arm of the horizontal
+//      sums; N does not depend on d, so the WTA compares V), running minimum
+//      with the smallest d on ties (Eq. 3) in registers across groups.
 // Finally the running best is merged with earlier passes and written.
-__global__ void __launch_bounds__(16 * 32) k_vagg(VArgs a)
+constexpr int kQS = 33;   // Q row stride: column d of consecutive rows hits distinct banks
+constexpr int kVSeg = 32; // rows per warp
+
+__host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)len * kQS + nw * 32 + 2 * len + nw; }
+
+__global__ void __launch_bounds__(16 * 32, 2) k_vagg(VArgs a)
 {
     extern __shared__ __align__(16) uint32_t vsmem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -280,104 +403,108 @@ __global__ void __launch_bounds__(16 * 32) k_vagg(VArgs a)
     const int x = blockIdx.x, view = blockIdx.y;
     const int ys = blockIdx.z * a.chunk, ye = min(H, ys + a.chunk);
     const int ya = max(0, ys - L1), yb = min(H, ye + L1);
-    const int len = yb - ya, seglog = a.seglog, seg = 1 << seglog;
-    uint32_t *Q = vsmem;                      // [len][32]
-    uint32_t *T = Q + len * 32;               // [nw][32]
-    uint32_t *NQ = T + nw * 32;               // [len]
+    const int len = yb - ya;
+    uint32_t *Q = vsmem;                      // [len][kQS]
+    uint32_t *T = Q + len * kQS;              // [nw][32] segment sums
+    uint32_t *NQ = T + nw * 32;               // [len] prefix of l + r + 1
     uint32_t *NT = NQ + len;                  // [nw]
     uint32_t *AW = NT + nw;                   // [len] arm words
-    uint32_t *BV = AW + len;                  // [len] running best aggregate
-    uint32_t *BD = BV + len;                  // [len] running best disparity
 
     const uint32_t *sh = (view ? a.sh[1] : a.sh[0]) + (size_t)x * a.dstride + lane;
     const uint32_t *arms = reinterpret_cast<const uint32_t *>(view ? a.arms[1] : a.arms[0]) + x;
     const size_t rowstride = (size_t)W * a.dstride;
-    const int sa = warp * seg, sb = min(len, sa + seg);   // relative to ya
+    const int sa = warp * kVSeg, sb = min(len, sa + kVSeg);   // relative to ya
     const int ng = (a.dc + 31) / 32;
     const bool want_vol = a.vol != nullptr && view == a.vol_view;
 
-    // arm words of the segment and the region-size prefix (d independent)
-    for (int r = sa + lane; r < sb; r += 32) cp_async4(AW + r, arms + (size_t)(ya + r) * W);
+    // arm word of this lane's row and the region-size prefix (d independent)
+    const int r = sa + lane;
+    const bool rin = r < sb;
+    const uint32_t aw = rin ? __ldg(arms + (size_t)(ya + r) * W) : 0u;
+    {
+        uint32_t nv = rin ? (aw & 0xffu) + ((aw >> 8) & 0xffu) + 1u : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {   // inclusive scan across the segment's rows
+            const uint32_t t = __shfl_up_sync(0xffffffffu, nv, o);
+            if (lane >= o) nv += t;
+        }
+        if (rin) { AW[r] = aw; NQ[r] = nv; }
+        if (lane == 31) NT[warp] = nv;
+    }
+    const bool out_row = rin && ya + r >= ys && ya + r < ye;
+    uint32_t bv = 0xffffffffu, bd = 0;
+
     for (int g = 0; g < ng; g++) {
-        // ---- A
-        for (int r = sa; r < sb; r++) cp_async4(Q + r * 32 + lane, sh + (size_t)(ya + r) * rowstride + g * 32);
-        cp_async_wait_all();
-        __syncwarp();
-        if (g == 0) {
-            uint32_t nrun = 0;
-            for (int r = sa; r < sb; r++) {
-                const uint32_t aw = AW[r];
-                nrun += (aw & 0xffu) + ((aw >> 8) & 0xffu) + 1u;
-                if (lane == 0) NQ[r] = nrun;
-            }
-            if (lane == 0) NT[warp] = nrun;
-        }
+        // ---- A: this warp's 32 rows of the slice column, lane = disparity
+        uint32_t v[kVSeg];
+        const uint32_t *src = sh + (size_t)(ya + sa) * rowstride + g * 32;
+#pragma unroll
+        for (int u = 0; u < kVSeg; u++) v[u] = sa + u < sb ? __ldg(src + (size_t)u * rowstride) : 0u;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int u = 0; u < kVSeg; u++) tot += v[u];
+        T[warp * 32 + lane] = tot;
+        __syncthreads();
         uint32_t run = 0;
-        for (int r = sa; r < sb; r++) {
-            run += Q[r * 32 + lane];
-            Q[r * 32 + lane] = run;
-        }
-        T[warp * 32 + lane] = run;
-        __syncthreads();
-        // ---- B
-        uint32_t offs = 0;
-        for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
-        if (warp > 0)
-            for (int r = sa; r < sb; r++) Q[r * 32 + lane] += offs;
+        for (int w = 0; w < warp; w++) run += T[w * 32 + lane];
         if (g == 0) {
-            uint32_t noffs = 0;
-            for (int w = 0; w < warp; w++) noffs += NT[w];
-            __syncwarp();
-            if (warp > 0)
-                for (int r = sa + lane; r < sb; r += 32) NQ[r] += noffs;
+            // region-size offsets (once)
+            uint32_t noff = 0;
+            for (int w = 0; w < warp; w++) noff += NT[w];
+            if (rin) NQ[r] += noff;
+        }
+        uint32_t *q = Q + sa * kQS + lane;
+#pragma unroll
+        for (int u = 0; u < kVSeg; u++) {
+            run += v[u];
+            if (sa + u < sb) q[u * kQS] = run;
         }
         __syncthreads();
-        // ---- C: rows of this warp's segment that are outputs
-        const int d = a.d0 + g * 32 + lane;
-        const bool live = g * 32 + lane < a.dc && d < a.D;
-        for (int r = max(sa, ys - ya); r < min(sb, ye - ya); r++) {
-            const uint32_t aw = AW[r];
+        // ---- C: lane = output row, loop over the group's disparities
+        const int dbase = a.d0 + g * 32;
+        const int nlive = max(0, min(32, min(a.dc - g * 32, a.D - dbase)));
+        if (out_row) {
             const int up = (aw >> 16) & 0xff, dn = aw >> 24;
-            const int hi = r + dn, lo = r - up - 1;   // lo >= -1
-            const uint32_t v = Q[hi * 32 + lane] - (lo >= 0 ? Q[lo * 32 + lane] : 0u);
-            const uint32_t vk = live ? v : 0xffffffffu;
-            const uint32_t vmin = __reduce_min_sync(0xffffffffu, vk);
-            const uint32_t dmin = __reduce_min_sync(0xffffffffu, (live && v == vmin) ? (uint32_t)d : 0xffffffffu);
-            if (lane == 0 && (g == 0 || vmin < BV[r])) {   // later groups hold larger d
-                BV[r] = vmin;
-                BD[r] = dmin;
+            const uint32_t *qh = Q + (r + dn) * kQS;
+            const int lo = r - up - 1;
+            const uint32_t *ql = Q + max(lo, 0) * kQS;
+            const uint32_t lomask = lo >= 0 ? 0xffffffffu : 0u;
+#pragma unroll 8
+            for (int j = 0; j < 32; j++) {
+                const uint32_t vv = qh[j] - (ql[j] & lomask);
+                if (j < nlive && vv < bv) { bv = vv; bd = (uint32_t)(dbase + j); }
             }
-            if (want_vol && live) {
-                const uint32_t n = NQ[hi] - (lo >= 0 ? NQ[lo] : 0u);
-                a.vol[((size_t)d * H + ya + r) * W + x] = float(v) / (float(n) * a.S);
+            if (want_vol) {
+                const uint32_t n = NQ[r + dn] - (lo >= 0 ? NQ[lo] : 0u);
+                for (int j = 0; j < nlive; j++) {
+                    const uint32_t vv = qh[j] - (ql[j] & lomask);
+                    a.vol[((size_t)(dbase + j) * H + ya + r) * W + x] = float(vv) / (float(n) * a.S);
+                }
             }
         }
         __syncthreads();   // Q and T are reused by the next group
     }
     // ---- merge with earlier passes, write the disparity (last pass) or state
+    if (!out_row) return;
     unsigned long long *best = view ? a.best[1] : a.best[0];
     int16_t *disp = view ? a.disp[1] : a.disp[0];
     float *cost = view ? a.cost[1] : a.cost[0];
-    for (int yo = ys + threadIdx.x; yo < ye; yo += blockDim.x) {
-        const int r = yo - ya;
-        const size_t i = (size_t)yo * W + x;
-        unsigned long long key = ((unsigned long long)BV[r] << 32) | BD[r];
-        if (!a.first) {
-            const unsigned long long prev = best[i];
-            key = prev <= key ? prev : key;   // earlier passes hold smaller d
+    const size_t i = (size_t)(ya + r) * W + x;
+    unsigned long long key = ((unsigned long long)bv << 32) | bd;
+    if (!a.first) {
+        const unsigned long long prev = best[i];
+        key = prev <= key ? prev : key;   // earlier passes hold smaller d
+    }
+    if (a.last) {
+        disp[i] = (int16_t)(key & 0xffffffffu);
+        if (cost) {
+            const int up = (aw >> 16) & 0xff, dn = aw >> 24;
+            const int lo = r - up - 1;
+            const uint32_t n = NQ[r + dn] - (lo >= 0 ? NQ[lo] : 0u);
+            cost[i] = float(uint32_t(key >> 32)) / (float(n) * a.S);
         }
-        if (a.last) {
-            disp[i] = (int16_t)(key & 0xffffffffu);
-            if (cost) {
-                const uint32_t aw = AW[r];
-                const int up = (aw >> 16) & 0xff, dn = aw >> 24;
-                const int hi = r + dn, lo = r - up - 1;
-                const uint32_t n = NQ[hi] - (lo >= 0 ? NQ[lo] : 0u);
-                cost[i] = float(uint32_t(key >> 32)) / (float(n) * a.S);
-            }
-        } else {
-            best[i] = key;
-        }
+    } else {
+        best[i] = key;
     }
 }
 
@@ -531,12 +658,13 @@ struct VGeom {
 VGeom vagg_geom(int W, int H, int L1)
 {
     VGeom g{};
-    const int nchunks = H <= kVMaxLen ? 1 : (H + 511) / 512;
+    // at most 16 warps of 32 rows: the prefix range (chunk + 2*L1) <= 512
+    const int nchunks = H <= 512 ? 1 : (H + (512 - 2 * kMaxL1) - 1) / (512 - 2 * kMaxL1);
     g.chunk = (H + nchunks - 1) / nchunks;
     const int len = std::min(H, g.chunk + 2 * L1);
-    g.seglog = 6;
-    g.nw = (len + (1 << g.seglog) - 1) >> g.seglog;
-    g.smem = ((size_t)len * 32 + (size_t)g.nw * 32 + len + g.nw + 3 * (size_t)len) * 4;
+    g.seglog = 5;   // 32 rows per warp, one output row per lane
+    g.nw = (len + kVSeg - 1) / kVSeg;
+    g.smem = vagg_smem_words(len, g.nw) * 4;
     g.grid = dim3(W, 2, nchunks);
     return g;
 }
@@ -698,7 +826,7 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
         }
         a.npx = npx;
         ProfScope ps(h, s, "k_pack");
-        k_pack<<<dim3((npx + 255) / 256, nimg), 256, 0, s>>>(a);
+        k_pack<<<dim3((npx / 4 + 256) / 256, nimg), 256, 0, s>>>(a);
         DCO_CUDA(h, cudaGetLastError());
     }
     PrepArgs a{};

@@ -88,7 +88,8 @@ def test_arms_bit_exact(env, k):
 def test_census_and_arms_other_windows(env):
     torch, binding, st = env
     img = scenes.config_scene(1).left
-    for cw, ch, l1, l2, t1, t2 in ((7, 5, 10, 4, 15, 5), (11, 5, 40, 20, 30, 8), (1, 1, 1, 0, 256, 256)):
+    for cw, ch, l1, l2, t1, t2 in ((7, 5, 10, 4, 15, 5), (11, 5, 40, 20, 30, 8), (1, 1, 1, 0, 256, 256),
+                                   (9, 7, 34, 17, 0, 6), (9, 7, 34, 2, 255, 0), (3, 3, 8, 8, 1, 1)):
         bp = binding.Params.default(census_w=cw, census_h=ch, arm_l1=l1, arm_l2=l2, tau1=t1, tau2=t2)
         got = st.census(dev(torch, img), bp).cpu().numpy().view(np.uint64)
         assert (got == O.census(img, cw, ch)).all()
