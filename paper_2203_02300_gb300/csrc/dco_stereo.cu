@@ -42,14 +42,13 @@ __device__ __forceinline__ uint32_t grey_of(uint32_t c)
     return (77u * (c & 0xffu) + 150u * ((c >> 8) & 0xffu) + 29u * ((c >> 16) & 0xffu) + 128u) >> 8;
 }
 
-__global__ void k_pack(PackArgs a)
+__device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   // pixels 4q .. 4q+3
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;   // pixels 4q .. 4q+3
     const int i0 = 4 * q;
     if (i0 >= a.npx) return;
-    const uint8_t *rgb = blockIdx.y ? a.rgb[1] : a.rgb[0];
-    uint32_t *rgbx = blockIdx.y ? a.rgbx[1] : a.rgbx[0];
-    uint8_t *grey = blockIdx.y ? a.grey[1] : a.grey[0];
+    const uint8_t *rgb = img ? a.rgb[1] : a.rgb[0];
+    uint32_t *rgbx = img ? a.rgbx[1] : a.rgbx[0];
+    uint8_t *grey = img ? a.grey[1] : a.grey[0];
     uint32_t c[4];
     if (i0 + 4 <= a.npx && ((reinterpret_cast<uintptr_t>(rgb) & 3u) == 0)) {
         const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * (size_t)i0);
@@ -100,25 +99,24 @@ __device__ __forceinline__ uint32_t lt4(uint32_t w, uint32_t c4)
 }
 
 template <int CW, int CH>
-__global__ void __launch_bounds__(kTX * kTY) k_prep(PrepArgs a)
+__device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int img)
 {
     __shared__ __align__(16) uint8_t gs[kTY + kMaxCH - 1][kGW];
-    const int img = blockIdx.z;
     const uint32_t *__restrict__ rgbx = img ? a.rgbx[1] : a.rgbx[0];
     const uint8_t *__restrict__ grey = img ? a.grey[1] : a.grey[0];
     const int W = a.W, H = a.H;
     const int cw = CW ? CW : a.cw, ch = CH ? CH : a.ch;
     const int rx = cw / 2, ry = ch / 2;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    for (int r = threadIdx.y; r < kTY + 2 * ry; r += kTY) {
+    const int x0 = bx * kTX, y0 = by * kTY;
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;   // 1-D block of kTX x kTY threads
+    for (int r = ty; r < kTY + 2 * ry; r += kTY) {
         const int y = min(max(y0 - ry + r, 0), H - 1);
-        for (int c = threadIdx.x; c < kTX + 2 * rx; c += kTX) {
+        for (int c = tx; c < kTX + 2 * rx; c += kTX) {
             const int x = min(max(x0 - rx + c, 0), W - 1);
             gs[r][c] = __ldg(grey + (size_t)y * W + x);
         }
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = x0 + tx, y = y0 + ty;
     if (x >= W || y >= H) return;
 
@@ -262,14 +260,14 @@ struct HSmem {
     }
 };
 
-__global__ void __launch_bounds__(16 * 32) k_hagg(HArgs a)
+__device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int W = a.W, L1 = a.L1;
-    const int y = blockIdx.y;
-    const int view = blockIdx.z / a.ngroups, g = blockIdx.z % a.ngroups;
-    const int xs = blockIdx.x * a.chunk, xe = min(W, xs + a.chunk);
+    const int y = by;
+    const int view = bz / a.ngroups, g = bz % a.ngroups;
+    const int xs = bx * a.chunk, xe = min(W, xs + a.chunk);
     const int xa = max(0, xs - L1), xb = min(W, xe + L1), len = xb - xa;
     const HSmem L(len, a.chunk, nw);
     float *sTA = reinterpret_cast<float *>(smem_raw);
@@ -395,13 +393,13 @@ constexpr int kVSeg = 32; // rows per warp
 
 __host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)len * kQS + nw * 32 + 2 * len + nw; }
 
-__global__ void __launch_bounds__(16 * 32, 2) k_vagg(VArgs a)
+__device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint32_t vsmem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int W = a.W, H = a.H, L1 = a.L1;
-    const int x = blockIdx.x, view = blockIdx.y;
-    const int ys = blockIdx.z * a.chunk, ye = min(H, ys + a.chunk);
+    const int x = bx, view = by;
+    const int ys = bz * a.chunk, ye = min(H, ys + a.chunk);
     const int ya = max(0, ys - L1), yb = min(H, ye + L1);
     const int len = yb - ya;
     uint32_t *Q = vsmem;                      // [len][kQS]
@@ -509,20 +507,87 @@ __global__ void __launch_bounds__(16 * 32, 2) k_vagg(VArgs a)
 }
 
 // ------------------------------------------------------------------ k_lr
-__global__ void k_lr(const int16_t *__restrict__ dl, const int16_t *__restrict__ dr, int W, int H,
-                     int tol, int16_t *__restrict__ out)
+__device__ __forceinline__ void lr_body(const LrArgs &a, size_t i)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)W * H) return;
-    const int x = int(i % W);
-    const int d = dl[i];
+    if (i >= (size_t)a.W * a.H) return;
+    const int x = int(i % a.W);
+    const int d = a.dl[i];
     int16_t r = -1;
-    if (tol < 0) r = (int16_t)d;
+    if (a.tol < 0) r = (int16_t)d;
     else if (d >= 0 && x - d >= 0) {
-        const int d2 = dr[i - d];
-        if (d2 >= 0 && abs(d - d2) <= tol) r = (int16_t)d;
+        const int d2 = a.dr[i - d];
+        if (d2 >= 0 && abs(d - d2) <= a.tol) r = (int16_t)d;
     }
-    out[i] = r;
+    a.out[i] = r;
+}
+
+// ------------------------------------------------------------------ batches
+// Every stage is one launch over all pairs of a batch (a single pair is a
+// batch of one).  The pairs' arguments travel in the kernel parameters; the
+// flat block index is mapped to (pair, block of that pair's own grid).
+template <class A, int N>
+struct Batch {
+    int n;
+    int off[N + 1];   // first flat block of each pair; off[n] = total
+    int gx[N], gy[N]; // the pair's own grid is gx x gy x gz
+    A p[N];
+};
+
+template <class A, int N>
+__device__ __forceinline__ int batch_pair(const Batch<A, N> &b, int flat, int &bx, int &by, int &bz)
+{
+    int lo = 0, hi = b.n - 1;
+    while (lo < hi) {   // last pair with off <= flat
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.off[mid] <= flat) lo = mid;
+        else hi = mid - 1;
+    }
+    const int local = flat - b.off[lo];
+    bx = local % b.gx[lo];
+    const int t = local / b.gx[lo];
+    by = t % b.gy[lo];
+    bz = t / b.gy[lo];
+    return lo;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Batch<PackArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    pack_body(b.p[i], bx * 256 + threadIdx.x, by);
+}
+
+template <int CW, int CH, int N>
+__global__ void __launch_bounds__(kTX * kTY) k_prep(const __grid_constant__ Batch<PrepArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    prep_body<CW, CH>(b.p[i], bx, by, bz);
+}
+
+template <int N>
+__global__ void __launch_bounds__(16 * 32) k_hagg(const __grid_constant__ Batch<HArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    hagg_body(b.p[i], bx, by, bz);
+}
+
+template <int N>
+__global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    vagg_body(b.p[i], bx, by, bz);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_lr(const __grid_constant__ Batch<LrArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    lr_body(b.p[i], (size_t)bx * 256 + threadIdx.x);
 }
 
 __global__ void k_extract_census(const uint4 *__restrict__ rec, int W, int H, int rpitch,
@@ -686,6 +751,7 @@ struct dco_stereo {
     size_t stage_cap = 0;
     bool profiling = false;
     unsigned long long launches = 0;
+    std::map<const void *, size_t> smem_set;   // dynamic shared memory opted in per kernel
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> pool;
     std::vector<ProfAgg> agg;
@@ -807,94 +873,231 @@ dco_status ensure_tables(dco_stereo *h, const dco_params &p, const Derived &dv, 
 template <class T>
 T *ws_ptr(dco_stereo *h, size_t off) { return reinterpret_cast<T *>(h->ws + off); }
 
-// first real record of row 0 of a padded record array
-uint4 *rec_ptr(dco_stereo *h, size_t off) { return ws_ptr<uint4>(h, off) + kRPad; }
 
 // grey/colour packing and census + arms for nimg images (1 or 2); arms of
 // image 0 go to arms0 (the caller's buffer for the arms entry point)
-dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, const Layout &L,
-                       const uint8_t *img0, const uint8_t *img1, int nimg, uchar4 *arms0, int W, int H,
-                       cudaStream_t s)
+// ----------------------------------------------------------- batched launches
+constexpr int kBatchMax = 64;   // pairs per launch (kernel parameter space)
+
+template <class A>
+struct Item {
+    A a;
+    int gx, gy, gz;   // the pair's own grid
+};
+
+template <class A, int N, class K>
+dco_status launch_group(dco_stereo *h, cudaStream_t s, const char *name, K kernel, const Item<A> *it, int n,
+                        int block, size_t smem)
 {
-    const int npx = W * H;
-    {
-        PackArgs a{};
-        a.rgb[0] = img0; a.rgb[1] = img1;
-        for (int v = 0; v < 2; v++) {
-            a.rgbx[v] = ws_ptr<uint32_t>(h, L.rgbx[v]);
-            a.grey[v] = ws_ptr<uint8_t>(h, L.grey[v]);
-        }
-        a.npx = npx;
-        ProfScope ps(h, s, "k_pack");
-        k_pack<<<dim3((npx / 4 + 256) / 256, nimg), 256, 0, s>>>(a);
-        DCO_CUDA(h, cudaGetLastError());
+    Batch<A, N> b;
+    std::memset(&b, 0, sizeof b);
+    b.n = n;
+    b.off[0] = 0;
+    for (int i = 0; i < n; i++) {
+        b.gx[i] = it[i].gx;
+        b.gy[i] = it[i].gy;
+        b.p[i] = it[i].a;
+        b.off[i + 1] = b.off[i] + it[i].gx * it[i].gy * it[i].gz;
     }
-    PrepArgs a{};
-    for (int v = 0; v < 2; v++) {
-        a.rgbx[v] = ws_ptr<uint32_t>(h, L.rgbx[v]);
-        a.grey[v] = ws_ptr<uint8_t>(h, L.grey[v]);
-        a.rec[v] = rec_ptr(h, L.rec[v]);
-        a.arms[v] = ws_ptr<uchar4>(h, L.arms[v]);
+    if (b.off[n] == 0) return DCO_OK;
+    // opt in once per size increase, so warmed-up calls make no attribute
+    // calls (safe inside stream capture)
+    size_t &done = h->smem_set[reinterpret_cast<const void *>(kernel)];
+    if (smem > (48u << 10) && smem > done) {
+        DCO_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        done = smem;
     }
-    if (arms0) a.arms[0] = arms0;
-    a.tables = h->d_tables;
-    a.W = W; a.H = H; a.rpitch = L.rpitch;
-    a.cw = p.census_w; a.ch = p.census_h;
-    a.L1 = dv.L1; a.L2 = p.arm_l2; a.tau1 = p.tau1; a.tau2 = p.tau2;
-    dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, nimg);
-    ProfScope ps(h, s, "k_prep");
-    if (p.census_w == 9 && p.census_h == 7) k_prep<9, 7><<<grid, dim3(kTX, kTY), 0, s>>>(a);
-    else k_prep<0, 0><<<grid, dim3(kTX, kTY), 0, s>>>(a);
+    ProfScope ps(h, s, name);
+    kernel<<<b.off[n], block, smem, s>>>(b);
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
 }
 
-dco_status launch_pass(dco_stereo *h, const Layout &L, const Derived &dv, int W, int H, int D, int d0,
-                       bool first, bool last, int16_t *disp_l, int16_t *disp_r, float *cost_l,
-                       float *cost_r, float *vol, int vol_view, cudaStream_t s)
+// one launch for a single pair (small parameter block), else groups of kBatchMax
+template <class A, class K1, class KN>
+dco_status launch_items(dco_stereo *h, cudaStream_t s, const char *name, K1 k1, KN kn,
+                        const std::vector<Item<A>> &items, int block, size_t smem)
 {
-    const int dc = std::min(L.dc, D - d0);
-    HArgs ha{};
-    for (int v = 0; v < 2; v++) {
-        ha.rec[v] = rec_ptr(h, L.rec[v]);
-        ha.arms[v] = ws_ptr<uchar4>(h, L.arms[v]);
-        ha.sh[v] = ws_ptr<uint32_t>(h, L.sh[v]);
-    }
-    ha.tables = h->d_tables;
-    ha.W = W; ha.H = H; ha.D = D; ha.rpitch = L.rpitch;
-    ha.d0 = d0; ha.dc = dc; ha.dstride = L.dstride;
-    ha.ngroups = (dc + 31) / 32;
-    ha.L1 = dv.L1; ha.S = dv.S; ha.Sint = dv.Sint;
-    {
-        const HGeom g = hagg_geom(W, H, dc, dv.L1);
-        ha.chunk = g.chunk;
-        ProfScope ps(h, s, "k_hagg");
-        cudaFuncSetAttribute(k_hagg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        k_hagg<<<g.grid, g.nw * 32, g.smem, s>>>(ha);
-        DCO_CUDA(h, cudaGetLastError());
-    }
-    VArgs va{};
-    for (int v = 0; v < 2; v++) {
-        va.sh[v] = ha.sh[v];
-        va.arms[v] = ha.arms[v];
-        va.best[v] = ws_ptr<unsigned long long>(h, L.best[v]);
-    }
-    va.disp[0] = disp_l; va.disp[1] = disp_r;
-    va.cost[0] = cost_l; va.cost[1] = cost_r;
-    va.vol = vol; va.vol_view = vol_view;
-    va.W = W; va.H = H; va.D = D; va.d0 = d0; va.dc = dc; va.dstride = L.dstride;
-    va.first = first; va.last = last;
-    va.L1 = dv.L1; va.S = dv.S;
-    {
-        const VGeom g = vagg_geom(W, H, dv.L1);
-        va.chunk = g.chunk;
-        va.seglog = g.seglog;
-        ProfScope ps(h, s, "k_vagg");
-        cudaFuncSetAttribute(k_vagg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        k_vagg<<<g.grid, g.nw * 32, g.smem, s>>>(va);
-        DCO_CUDA(h, cudaGetLastError());
+    if (items.empty()) return DCO_OK;
+    if (items.size() == 1) return launch_group<A, 1>(h, s, name, k1, items.data(), 1, block, smem);
+    for (size_t i = 0; i < items.size(); i += kBatchMax) {
+        const int n = (int)std::min<size_t>(kBatchMax, items.size() - i);
+        dco_status st = launch_group<A, kBatchMax>(h, s, name, kn, items.data() + i, n, block, smem);
+        if (st != DCO_OK) return st;
     }
     return DCO_OK;
+}
+
+// one pair of a run
+struct Job {
+    const uint8_t *left = nullptr, *right = nullptr;
+    int W = 0, H = 0, D = 0;
+    int16_t *out = nullptr, *disp_l = nullptr, *disp_r = nullptr;
+    float *cost_l = nullptr, *cost_r = nullptr, *vol = nullptr;
+    int vol_view = 0;
+    uchar4 *arms0 = nullptr;   // stage entry point: arms of image 0 go here
+    Layout L{};
+    size_t base = 0;           // workspace offset of this pair
+};
+
+// workspace plan for all jobs; the pass width shrinks (same for all pairs)
+// until the plan fits the handle's budget
+dco_status plan_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, size_t &total)
+{
+    auto plan = [&](int dc_override) {
+        size_t t = 0;
+        for (auto &j : jobs) {
+            j.L = make_layout(j.W, j.H, j.D, p, dc_override);
+            j.base = t;
+            t = align_up(t + j.L.total);
+        }
+        return t;
+    };
+    total = plan(0);
+    if (h->budget && total > h->budget) {
+        int widest = 32;
+        for (auto &j : jobs) widest = std::max(widest, (j.L.dc + 31) / 32 * 32);
+        for (int dc = widest; dc >= 32 && total > h->budget; dc -= 32) total = plan(dc);
+    }
+    return DCO_OK;
+}
+
+template <class T>
+T *jptr(dco_stereo *h, const Job &j, size_t off) { return ws_ptr<T>(h, j.base + off); }
+
+// grey/colour packing and census + arms for nimg images of every job
+dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, const std::vector<Job> &jobs,
+                       int nimg, cudaStream_t s)
+{
+    std::vector<Item<PackArgs>> pk;
+    std::vector<Item<PrepArgs>> pr;
+    for (const Job &j : jobs) {
+        const int npx = j.W * j.H;
+        Item<PackArgs> a{};
+        a.a.rgb[0] = j.left; a.a.rgb[1] = j.right;
+        for (int v = 0; v < 2; v++) {
+            a.a.rgbx[v] = jptr<uint32_t>(h, j, j.L.rgbx[v]);
+            a.a.grey[v] = jptr<uint8_t>(h, j, j.L.grey[v]);
+        }
+        a.a.npx = npx;
+        a.gx = (npx + 1023) / 1024;   // 256 threads x 4 pixels
+        a.gy = nimg;
+        a.gz = 1;
+        pk.push_back(a);
+        Item<PrepArgs> b{};
+        for (int v = 0; v < 2; v++) {
+            b.a.rgbx[v] = jptr<uint32_t>(h, j, j.L.rgbx[v]);
+            b.a.grey[v] = jptr<uint8_t>(h, j, j.L.grey[v]);
+            b.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
+            b.a.arms[v] = jptr<uchar4>(h, j, j.L.arms[v]);
+        }
+        if (j.arms0) b.a.arms[0] = j.arms0;
+        b.a.tables = h->d_tables;
+        b.a.W = j.W; b.a.H = j.H; b.a.rpitch = j.L.rpitch;
+        b.a.cw = p.census_w; b.a.ch = p.census_h;
+        b.a.L1 = dv.L1; b.a.L2 = p.arm_l2; b.a.tau1 = p.tau1; b.a.tau2 = p.tau2;
+        b.gx = (j.W + kTX - 1) / kTX;
+        b.gy = (j.H + kTY - 1) / kTY;
+        b.gz = nimg;
+        pr.push_back(b);
+    }
+    dco_status st = launch_items(h, s, "k_pack", k_pack<1>, k_pack<kBatchMax>, pk, 256, 0);
+    if (st != DCO_OK) return st;
+    if (p.census_w == 9 && p.census_h == 7)
+        return launch_items(h, s, "k_prep", k_prep<9, 7, 1>, k_prep<9, 7, kBatchMax>, pr, kTX * kTY, 0);
+    return launch_items(h, s, "k_prep", k_prep<0, 0, 1>, k_prep<0, 0, kBatchMax>, pr, kTX * kTY, 0);
+}
+
+// pass `pass` (disparities [pass*dc, pass*dc + dc)) of every job that has it
+dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> &jobs, int pass, cudaStream_t s)
+{
+    std::vector<Item<HArgs>> hi;
+    std::vector<Item<VArgs>> vi;
+    int hnw = 1, vnw = 1;
+    for (const Job &j : jobs) {
+        if (pass >= j.L.npass) continue;
+        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
+        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
+        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
+        hnw = std::max(hnw, hg.nw);
+        vnw = std::max(vnw, vg.nw);
+    }
+    size_t hsmem = 0, vsmem = 0;
+    for (const Job &j : jobs) {
+        if (pass >= j.L.npass) continue;
+        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
+        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
+        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
+        const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
+        hsmem = std::max(hsmem, (size_t)HSmem(hlen, hg.chunk, hnw).total);
+        vsmem = std::max(vsmem, vagg_smem_words(vlen, vnw) * 4);
+        Item<HArgs> a{};
+        for (int v = 0; v < 2; v++) {
+            a.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
+            a.a.arms[v] = jptr<uchar4>(h, j, j.L.arms[v]);
+            a.a.sh[v] = jptr<uint32_t>(h, j, j.L.sh[v]);
+        }
+        a.a.tables = h->d_tables;
+        a.a.W = j.W; a.a.H = j.H; a.a.D = j.D; a.a.rpitch = j.L.rpitch;
+        a.a.d0 = d0; a.a.dc = dc; a.a.dstride = j.L.dstride;
+        a.a.ngroups = (dc + 31) / 32;
+        a.a.L1 = dv.L1; a.a.chunk = hg.chunk; a.a.S = dv.S; a.a.Sint = dv.Sint;
+        a.gx = hg.grid.x; a.gy = hg.grid.y; a.gz = hg.grid.z;
+        hi.push_back(a);
+        Item<VArgs> b{};
+        for (int v = 0; v < 2; v++) {
+            b.a.sh[v] = a.a.sh[v];
+            b.a.arms[v] = a.a.arms[v];
+            b.a.best[v] = jptr<unsigned long long>(h, j, j.L.best[v]);
+        }
+        b.a.disp[0] = j.disp_l; b.a.disp[1] = j.disp_r;
+        b.a.cost[0] = j.cost_l; b.a.cost[1] = j.cost_r;
+        b.a.vol = j.vol; b.a.vol_view = j.vol_view;
+        b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
+        b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
+        b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        b.gx = vg.grid.x; b.gy = vg.grid.y; b.gz = vg.grid.z;
+        vi.push_back(b);
+    }
+    dco_status st = launch_items(h, s, "k_hagg", k_hagg<1>, k_hagg<kBatchMax>, hi, hnw * 32, hsmem);
+    if (st != DCO_OK) return st;
+    return launch_items(h, s, "k_vagg", k_vagg<1>, k_vagg<kBatchMax>, vi, vnw * 32, vsmem);
+}
+
+dco_status launch_lr(dco_stereo *h, const std::vector<Item<LrArgs>> &items, cudaStream_t s)
+{
+    return launch_items(h, s, "k_lr", k_lr<1>, k_lr<kBatchMax>, items, 256, 0);
+}
+
+// the whole path for a set of independent pairs: one launch per stage
+dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, cudaStream_t s)
+{
+    Derived dv;
+    derive(p, dv);
+    size_t total = 0;
+    dco_status st = plan_jobs(h, p, jobs, total);
+    if (st != DCO_OK) return st;
+    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+    int maxpass = 0;
+    for (Job &j : jobs) {
+        if (!j.disp_l) j.disp_l = jptr<int16_t>(h, j, j.L.disp[0]);
+        if (!j.disp_r) j.disp_r = jptr<int16_t>(h, j, j.L.disp[1]);
+        maxpass = std::max(maxpass, j.L.npass);
+    }
+    if ((st = launch_prep(h, p, dv, jobs, 2, s)) != DCO_OK) return st;
+    for (int pass = 0; pass < maxpass; pass++)
+        if ((st = launch_pass(h, dv, jobs, pass, s)) != DCO_OK) return st;
+    std::vector<Item<LrArgs>> lr;
+    for (const Job &j : jobs) {
+        if (!j.out) continue;
+        Item<LrArgs> it{};
+        it.a.dl = j.disp_l; it.a.dr = j.disp_r; it.a.out = j.out;
+        it.a.W = j.W; it.a.H = j.H; it.a.tol = p.lr_tol;
+        it.gx = (j.W * j.H + 255) / 256; it.gy = 1; it.gz = 1;
+        lr.push_back(it);
+    }
+    return launch_lr(h, lr, s);
 }
 
 dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
@@ -914,36 +1117,12 @@ dco_status run_match(dco_stereo *h, const uint8_t *left, const uint8_t *right, i
                      const dco_params &p, int16_t *disp_out, int16_t *disp_l, int16_t *disp_r,
                      float *cost_l, float *cost_r, float *vol, int vol_view, cudaStream_t s)
 {
-    Derived dv;
-    derive(p, dv);
-    Layout L = make_layout(W, H, D, p);
-    if (h->budget && L.total > h->budget) {
-        // shrink the pass until the slices fit
-        for (int dc = (L.dc / 32) * 32; dc >= 32; dc -= 32) {
-            Layout L2 = make_layout(W, H, D, p, dc);
-            if (L2.total <= h->budget) { L = L2; break; }
-        }
-    }
-    dco_status st = ensure_ws(h, L.total);
-    if (st != DCO_OK) return st;
-    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
-    if (!disp_l) disp_l = ws_ptr<int16_t>(h, L.disp[0]);
-    if (!disp_r) disp_r = ws_ptr<int16_t>(h, L.disp[1]);
-    if ((st = launch_prep(h, p, dv, L, left, right, 2, nullptr, W, H, s)) != DCO_OK)
-        return st;
-    for (int d0 = 0; d0 < D; d0 += L.dc) {
-        const bool first = d0 == 0, last = d0 + L.dc >= D;
-        if ((st = launch_pass(h, L, dv, W, H, D, d0, first, last, disp_l, disp_r, cost_l, cost_r, vol,
-                              vol_view, s)) != DCO_OK)
-            return st;
-    }
-    if (disp_out) {
-        const size_t n = (size_t)W * H;
-        ProfScope ps(h, s, "k_lr");
-        k_lr<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(disp_l, disp_r, W, H, p.lr_tol, disp_out);
-        DCO_CUDA(h, cudaGetLastError());
-    }
-    return DCO_OK;
+    std::vector<Job> jobs(1);
+    Job &j = jobs[0];
+    j.left = left; j.right = right; j.W = W; j.H = H; j.D = D;
+    j.out = disp_out; j.disp_l = disp_l; j.disp_r = disp_r;
+    j.cost_l = cost_l; j.cost_r = cost_r; j.vol = vol; j.vol_view = vol_view;
+    return run_jobs(h, p, jobs, s);
 }
 
 } // namespace
@@ -1091,6 +1270,24 @@ dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host, const 
     return DCO_OK;
 }
 
+// census + arms of one image (stage entry points): the pack/prep launches
+// of a one-job run with a single image
+static dco_status prep_one(dco_stereo *h, const dco_params &p, const uint8_t *rgb, int W, int H,
+                           uchar4 *arms_out, std::vector<Job> &jobs, cudaStream_t s)
+{
+    Derived dv;
+    derive(p, dv);
+    jobs.assign(1, Job{});
+    Job &j = jobs[0];
+    j.left = rgb; j.right = rgb; j.W = W; j.H = H; j.D = 1; j.arms0 = arms_out;
+    size_t total = 0;
+    dco_status st = plan_jobs(h, p, jobs, total);
+    if (st != DCO_OK) return st;
+    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+    return launch_prep(h, p, dv, jobs, 1, s);
+}
+
 dco_status dco_stereo_census(dco_stereo *h, const uint8_t *rgb, int W, int H, const dco_params *pin,
                              uint64_t *census_out, dco_stream stream)
 {
@@ -1098,17 +1295,14 @@ dco_status dco_stereo_census(dco_stereo *h, const uint8_t *rgb, int W, int H, co
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
     if (!rgb || !census_out || !dims_valid(W, H, 1)) return DCO_EINVAL;
-    Derived dv;
-    derive(p, dv);
-    Layout L = make_layout(W, H, 1, p);
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_ws(h, L.total)) != DCO_OK) return st;
-    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
-    if ((st = launch_prep(h, p, dv, L, rgb, rgb, 1, nullptr, W, H, s)) != DCO_OK)
-        return st;
+    std::vector<Job> jobs;
+    if ((st = prep_one(h, p, rgb, W, H, nullptr, jobs, s)) != DCO_OK) return st;
+    const Job &j = jobs[0];
     const size_t n = (size_t)W * H;
     ProfScope ps(h, s, "k_extract_census");
-    k_extract_census<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec_ptr(h, L.rec[0]), W, H, L.rpitch,
+    k_extract_census<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(jptr<uint4>(h, j, j.L.rec[0]) + kRPad, W, H,
+                                                                  j.L.rpitch,
                                                                   reinterpret_cast<unsigned long long *>(census_out));
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
@@ -1121,15 +1315,8 @@ dco_status dco_stereo_arms(dco_stereo *h, const uint8_t *rgb, int W, int H, cons
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
     if (!rgb || !arms_out || !dims_valid(W, H, 1)) return DCO_EINVAL;
-    Derived dv;
-    derive(p, dv);
-    Layout L = make_layout(W, H, 1, p);
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_ws(h, L.total)) != DCO_OK) return st;
-    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
-    if ((st = launch_prep(h, p, dv, L, rgb, rgb, 1, reinterpret_cast<uchar4 *>(arms_out), W, H, s)) != DCO_OK)
-        return st;
-    return DCO_OK;
+    std::vector<Job> jobs;
+    return prep_one(h, p, rgb, W, H, reinterpret_cast<uchar4 *>(arms_out), jobs, (cudaStream_t)stream);
 }
 
 dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H,
@@ -1148,12 +1335,11 @@ dco_status dco_stereo_lr_check(dco_stereo *h, const int16_t *dl, const int16_t *
 {
     if (!h || !dl || !dr || !out || W < 1 || H < 1) return DCO_EINVAL;
     DCO_CUDA(h, cudaSetDevice(h->device));
-    const size_t n = (size_t)W * H;
-    cudaStream_t s = (cudaStream_t)stream;
-    ProfScope ps(h, s, "k_lr");
-    k_lr<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dl, dr, W, H, tol, out);
-    DCO_CUDA(h, cudaGetLastError());
-    return DCO_OK;
+    std::vector<Item<LrArgs>> it(1);
+    it[0].a.dl = dl; it[0].a.dr = dr; it[0].a.out = out;
+    it[0].a.W = W; it[0].a.H = H; it[0].a.tol = tol;
+    it[0].gx = (int)(((size_t)W * H + 255) / 256); it[0].gy = 1; it[0].gz = 1;
+    return launch_lr(h, it, (cudaStream_t)stream);
 }
 
 dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int n, const dco_params *pin,
@@ -1167,12 +1353,14 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
         if (!descs[i].left || !descs[i].right || !descs[i].disp_out ||
             !dims_valid(descs[i].W, descs[i].H, descs[i].D))
             return DCO_EINVAL;
+    if (n == 0) return DCO_OK;
+    std::vector<Job> jobs(n);
     for (int i = 0; i < n; i++) {
-        st = run_match(h, descs[i].left, descs[i].right, descs[i].W, descs[i].H, descs[i].D, p,
-                       descs[i].disp_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0, (cudaStream_t)stream);
-        if (st != DCO_OK) return st;
+        jobs[i].left = descs[i].left; jobs[i].right = descs[i].right;
+        jobs[i].W = descs[i].W; jobs[i].H = descs[i].H; jobs[i].D = descs[i].D;
+        jobs[i].out = descs[i].disp_out;
     }
-    return DCO_OK;
+    return run_jobs(h, p, jobs, (cudaStream_t)stream);
 }
 
 dco_status dco_stereo_sync_status(dco_stereo *h)

@@ -90,4 +90,10 @@ struct VArgs {
     float S;
 };
 
+struct LrArgs {
+    const int16_t *dl, *dr;
+    int16_t *out;
+    int W, H, tol;
+};
+
 } // namespace dco

@@ -1,0 +1,133 @@
+"""Batched path (config 3: 32 pairs of uneven W x H x D in one pass of the
+pipeline, one launch per stage) and its CUDA-graph replay.
+
+The batched kernels run the same per-pair code as the single-pair path, so a
+pair's disparity map must be bit-identical alone and inside a batch; a few
+pairs are also checked against the oracle under the parity rule.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2203_02300_gb300 import scenes
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_02300_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    st = binding.Stereo(0)
+    yield torch, binding, st
+    st.close()
+
+
+@pytest.fixture(scope="module")
+def config3():
+    return scenes.batch_config3(32)
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _single(env, s, params=None):
+    torch, binding, st = env
+    return st.match(_dev(torch, s.left), _dev(torch, s.right), s.D, params).cpu().numpy()
+
+
+def test_config3_batch_equals_single(env, config3):
+    torch, binding, st = env
+    pairs = []
+    for s in config3:
+        L, R = _dev(torch, s.left), _dev(torch, s.right)
+        pairs.append((L, R, s.D, torch.full((s.H, s.W), -9, dtype=torch.int16, device="cuda")))
+    st.match_batch(pairs)
+    torch.cuda.synchronize()
+    st.sync_status()
+    sizes = set()
+    for s, (_, _, _, out) in zip(config3, pairs):
+        sizes.add((s.W, s.H, s.D))
+        assert np.array_equal(out.cpu().numpy(), _single(env, s)), (s.W, s.H, s.D)
+    assert len(sizes) >= 3   # the batch really is uneven
+
+
+def test_config3_batch_parity_sampled(env, config3):
+    # every distinct shape once, oracle on a top band and a middle band
+    torch, binding, st = env
+    seen = {}
+    for s in config3:
+        seen.setdefault((s.W, s.H, s.D), s)
+    pairs = []
+    for s in seen.values():
+        pairs.append((_dev(torch, s.left), _dev(torch, s.right), s.D,
+                      torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")))
+    st.match_batch(pairs)
+    torch.cuda.synchronize()
+    for s, (_, _, _, out) in zip(seen.values(), pairs):
+        got = out.cpu().numpy()
+        for rows in ((0, 4), (s.H // 2, s.H // 2 + 4)):
+            ref = O.match(s.left, s.right, s.D, rows=rows)
+            g = got[rows[0]:rows[1]]
+            keep = (g >= 0) & (ref.disp >= 0)
+            parity.check_disparity(g[keep], ref.disp[keep], ref.best_l[keep], ref.second_l[keep],
+                                   f"batch {s.W}x{s.H} D={s.D}")
+            # validity agrees with the oracle's consistency check almost everywhere
+            assert ((g >= 0) != (ref.disp >= 0)).mean() <= 2 * parity.MAX_EXCUSED
+
+
+def test_more_pairs_than_one_launch_holds(env):
+    # 70 small pairs: two launch groups per stage (64 + 6)
+    torch, binding, st = env
+    ss = [scenes.plane_scene(72 + (i % 5) * 8, 40 + (i % 3) * 8, 16 + (i % 2) * 8, 3,
+                             seed=scenes.seed_for(3, 500 + i), drange=(1, 14)) for i in range(70)]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")) for s in ss]
+    st.match_batch(pairs)
+    torch.cuda.synchronize()
+    for s, (_, _, _, out) in zip(ss, pairs):
+        assert np.array_equal(out.cpu().numpy(), _single(env, s))
+
+
+def test_batch_with_several_passes(env, config3):
+    torch, binding, st = env
+    p = binding.Params.default(d_chunk=32)
+    sub = config3[:8]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")) for s in sub]
+    st.match_batch(pairs, p)
+    torch.cuda.synchronize()
+    for s, (_, _, _, out) in zip(sub, pairs):
+        assert np.array_equal(out.cpu().numpy(), _single(env, s))
+
+
+def test_graph_replay_matches_direct_calls(env, config3):
+    torch, binding, st = env
+    from paper_2203_02300_gb300.batch import BatchGraph
+    sub = config3[:6]
+    g = BatchGraph(binding.Stereo(0), [(s.W, s.H, s.D) for s in sub])
+    # second set: same shapes, different scenes, so a replay that ignored its
+    # new inputs would fail
+    other = [scenes.plane_scene(s.W, s.H, s.D, 5, seed=scenes.seed_for(3, 900 + i), drange=(2, s.D - 2),
+                                noise_sigma=2.0) for i, s in enumerate(sub)]
+    for batch in (sub, other, sub):
+        outs = g([_dev(torch, s.left) for s in batch], [_dev(torch, s.right) for s in batch])
+        torch.cuda.synchronize()
+        for s, out in zip(batch, outs):
+            assert np.array_equal(out.cpu().numpy(), _single(env, s))
+
+
+def test_empty_and_invalid_batches(env):
+    torch, binding, st = env
+    st.match_batch([])
+    L = torch.zeros((8, 8, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((8, 8), dtype=torch.int16, device="cuda")
+    with pytest.raises(binding.DcoError) as e:
+        st.match_batch([(L, L, 9, out)])   # D > W
+    assert e.value.code == binding.DCO_EINVAL
