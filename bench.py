@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the config 3 batch and config 4 serving runs")
     return ap.parse_args()
 
 
@@ -278,6 +279,13 @@ def own_arm(args):
             "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
             if src == "measured" else "fallback 6.8 TB/s"}
 
+    # ---- config 3 (batched) and config 4 (serving), rank 0 only
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
+        extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
+        extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
+
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -305,10 +313,85 @@ def own_arm(args):
             "wall_s_timed_region": t_wall,
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line))
     st.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- config 3 and config 4
+def batch_config3(torch, binding, st, flush, dev, reps: int = 10):
+    """32 pairs of uneven size: one batched pass (CUDA-graph replay) against
+    the same pairs matched one call at a time; L2 flushed before each."""
+    from paper_2203_02300_gb300 import scenes
+    from paper_2203_02300_gb300.batch import BatchGraph
+    sc = scenes.batch_config3(32)
+    L = [torch.from_numpy(s.left).to(dev) for s in sc]
+    R = [torch.from_numpy(s.right).to(dev) for s in sc]
+    outs = [torch.empty((s.H, s.W), dtype=torch.int16, device=dev) for s in sc]
+    units = sum(s.W * s.H * s.D for s in sc)
+    g = BatchGraph(binding.Stereo(dev.index or 0), [(s.W, s.H, s.D) for s in sc], device=dev.index or 0)
+    g.load(L, R)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        ms = []
+        for _ in range(reps + 2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms[2:])
+
+    def sequential():
+        for l, r, s, o in zip(L, R, sc, outs):
+            st.match(l, r, s.D, None, o)
+
+    def batched():
+        g.replay()   # launched on the current stream, ordered after the flush
+
+    t_seq = timed(sequential)
+    t_bat = timed(batched)
+    same = all(torch.equal(a, b) for a, b in zip(outs, g.out))
+    sizes = sorted({(s.W, s.H, s.D) for s in sc})
+    return {"pairs": len(sc), "sizes": [f"{w}x{h} D={d}" for w, h, d in sizes], "evals": units,
+            "batched_graph_ms": t_bat, "batched_evals_per_s": units / (t_bat * 1e-3),
+            "sequential_ms": t_seq, "sequential_evals_per_s": units / (t_seq * 1e-3),
+            "speedup": t_seq / t_bat, "identical_to_sequential": bool(same)}
+
+
+def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0):
+    """4 camera streams, 300 frames each, Poisson arrivals at 30 Hz (real
+    time): continuous batching over two lanes; p50/p99 from arrival to map on
+    the host, against one plain synchronous call per frame size."""
+    import numpy as np
+    from paper_2203_02300_gb300 import scenes
+    from paper_2203_02300_gb300.serve import run_config4
+    stats, outs, frames = run_config4(frames_per_stream=300, rate_hz=30.0, unique_frames=4, device=device,
+                                      time_scale=time_scale)
+    plain = {}
+    for i, (W, H, D) in enumerate(scenes.STREAMS_CONFIG4):
+        l, r = frames[i][0]
+        outh = np.empty((H, W), np.int16)
+        for _ in range(3):
+            st.match_host(l.numpy(), r.numpy(), D, out=outh)
+        ts = []
+        for _ in range(20):
+            t0 = time.perf_counter()
+            st.match_host(l.numpy(), r.numpy(), D, out=outh)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        plain[f"{W}x{H} D={D}"] = {"p50_ms": statistics.median(ts), "p99_ms": max(ts)}
+        assert np.array_equal(outh, outs[(i, 0)]), "served map differs from the plain call"
+    stats = dict(stats)
+    stats["per_stream"] = {f"{W}x{H} D={D}": v for (W, H, D), (k, v) in
+                           zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
+    return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
+            "frames_per_stream": 300, "rate_hz": 30 * time_scale, **stats, "plain_single_call": plain}
 
 
 # ------------------------------------------------------- oracle timing

@@ -751,7 +751,6 @@ struct dco_stereo {
     size_t stage_cap = 0;
     bool profiling = false;
     unsigned long long launches = 0;
-    std::map<const void *, size_t> smem_set;   // dynamic shared memory opted in per kernel
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> pool;
     std::vector<ProfAgg> agg;
@@ -879,6 +878,23 @@ T *ws_ptr(dco_stereo *h, size_t off) { return reinterpret_cast<T *>(h->ws + off)
 // ----------------------------------------------------------- batched launches
 constexpr int kBatchMax = 64;   // pairs per launch (kernel parameter space)
 
+// The dynamic shared-memory limit is an attribute of the kernel on a device,
+// shared by every handle and thread of the process: it is raised under a lock
+// and never lowered, so a warmed-up process makes no attribute calls (safe
+// inside stream capture) and no handle can shrink another's limit.
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void *>, size_t> g_smem_set;
+
+dco_status opt_in_smem(dco_stereo *h, const void *kernel, size_t smem)
+{
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    size_t &done = g_smem_set[{h->device, kernel}];
+    if (smem <= done) return DCO_OK;
+    DCO_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    done = smem;
+    return DCO_OK;
+}
+
 template <class A>
 struct Item {
     A a;
@@ -900,16 +916,19 @@ dco_status launch_group(dco_stereo *h, cudaStream_t s, const char *name, K kerne
         b.off[i + 1] = b.off[i] + it[i].gx * it[i].gy * it[i].gz;
     }
     if (b.off[n] == 0) return DCO_OK;
-    // opt in once per size increase, so warmed-up calls make no attribute
-    // calls (safe inside stream capture)
-    size_t &done = h->smem_set[reinterpret_cast<const void *>(kernel)];
-    if (smem > (48u << 10) && smem > done) {
-        DCO_CUDA(h, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        done = smem;
+    if (smem > (48u << 10)) {
+        dco_status st = opt_in_smem(h, reinterpret_cast<const void *>(kernel), smem);
+        if (st != DCO_OK) return st;
     }
     ProfScope ps(h, s, name);
     kernel<<<b.off[n], block, smem, s>>>(b);
-    DCO_CUDA(h, cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->last_error = std::string(name) + " launch (" + std::to_string(n) + " pairs, " + std::to_string(b.off[n]) +
+                        " blocks of " + std::to_string(block) + " threads, " + std::to_string(smem) +
+                        " B shared): " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DCO_ENOMEM : DCO_ECUDA;
+    }
     return DCO_OK;
 }
 
@@ -1008,29 +1027,22 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
     return launch_items(h, s, "k_prep", k_prep<0, 0, 1>, k_prep<0, 0, kBatchMax>, pr, kTX * kTY, 0);
 }
 
-// pass `pass` (disparities [pass*dc, pass*dc + dc)) of every job that has it
+// pass `pass` (disparities [pass*dc, pass*dc + dc)) of every job that has it.
+// Pairs are bucketed by block size (warps per block) so no block carries
+// idle warps for a larger pair; one launch per bucket and stage.
 dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> &jobs, int pass, cudaStream_t s)
 {
-    std::vector<Item<HArgs>> hi;
-    std::vector<Item<VArgs>> vi;
-    int hnw = 1, vnw = 1;
-    for (const Job &j : jobs) {
-        if (pass >= j.L.npass) continue;
-        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
-        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
-        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
-        hnw = std::max(hnw, hg.nw);
-        vnw = std::max(vnw, vg.nw);
-    }
-    size_t hsmem = 0, vsmem = 0;
+    std::map<int, std::vector<Item<HArgs>>> hb;
+    std::map<int, std::vector<Item<VArgs>>> vb;
+    std::map<int, size_t> hsm, vsm;
     for (const Job &j : jobs) {
         if (pass >= j.L.npass) continue;
         const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
         const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
         const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
         const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
-        hsmem = std::max(hsmem, (size_t)HSmem(hlen, hg.chunk, hnw).total);
-        vsmem = std::max(vsmem, vagg_smem_words(vlen, vnw) * 4);
+        hsm[hg.nw] = std::max(hsm[hg.nw], (size_t)HSmem(hlen, hg.chunk, hg.nw).total);
+        vsm[vg.nw] = std::max(vsm[vg.nw], vagg_smem_words(vlen, vg.nw) * 4);
         Item<HArgs> a{};
         for (int v = 0; v < 2; v++) {
             a.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
@@ -1043,7 +1055,7 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         a.a.ngroups = (dc + 31) / 32;
         a.a.L1 = dv.L1; a.a.chunk = hg.chunk; a.a.S = dv.S; a.a.Sint = dv.Sint;
         a.gx = hg.grid.x; a.gy = hg.grid.y; a.gz = hg.grid.z;
-        hi.push_back(a);
+        hb[hg.nw].push_back(a);
         Item<VArgs> b{};
         for (int v = 0; v < 2; v++) {
             b.a.sh[v] = a.a.sh[v];
@@ -1057,11 +1069,19 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
         b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
         b.gx = vg.grid.x; b.gy = vg.grid.y; b.gz = vg.grid.z;
-        vi.push_back(b);
+        vb[vg.nw].push_back(b);
     }
-    dco_status st = launch_items(h, s, "k_hagg", k_hagg<1>, k_hagg<kBatchMax>, hi, hnw * 32, hsmem);
-    if (st != DCO_OK) return st;
-    return launch_items(h, s, "k_vagg", k_vagg<1>, k_vagg<kBatchMax>, vi, vnw * 32, vsmem);
+    for (auto &kv : hb) {
+        dco_status st = launch_items(h, s, "k_hagg", k_hagg<1>, k_hagg<kBatchMax>, kv.second, kv.first * 32,
+                                     hsm[kv.first]);
+        if (st != DCO_OK) return st;
+    }
+    for (auto &kv : vb) {
+        dco_status st = launch_items(h, s, "k_vagg", k_vagg<1>, k_vagg<kBatchMax>, kv.second, kv.first * 32,
+                                     vsm[kv.first]);
+        if (st != DCO_OK) return st;
+    }
+    return DCO_OK;
 }
 
 dco_status launch_lr(dco_stereo *h, const std::vector<Item<LrArgs>> &items, cudaStream_t s)

@@ -191,19 +191,29 @@ class Server:
                     self.cv.wait(0.001)
                     continue
                 lane.busy = True
-            with torch.cuda.stream(lane.stream):
-                pairs = []
-                for r in batch:
-                    sl = self.slots[r.stream][r.slot]
-                    sl.left.copy_(r.left, non_blocking=True)
-                    sl.right.copy_(r.right, non_blocking=True)
-                    pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out))
-                lane.stereo.match_batch(pairs, self.params, stream=lane.stream)
-                for r in batch:
-                    sl = self.slots[r.stream][r.slot]
-                    sl.host_out.copy_(sl.out, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(lane.stream)
+            try:
+                with torch.cuda.stream(lane.stream):
+                    pairs = []
+                    for r in batch:
+                        sl = self.slots[r.stream][r.slot]
+                        sl.left.copy_(r.left, non_blocking=True)
+                        sl.right.copy_(r.right, non_blocking=True)
+                        pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out))
+                    lane.stereo.match_batch(pairs, self.params, stream=lane.stream)
+                    for r in batch:
+                        sl = self.slots[r.stream][r.slot]
+                        sl.host_out.copy_(sl.out, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(lane.stream)
+            except Exception as exc:   # fail this batch's requests, keep serving
+                lane.stream.synchronize()
+                with self.cv:
+                    for r in batch:
+                        self.slots[r.stream][r.slot].busy = False
+                        r.future.set_exception(exc)
+                    lane.busy = False
+                    self.cv.notify_all()
+                continue
             self.n_batches += 1
             self.n_frames_batched += len(batch)
             with self.done_cv:

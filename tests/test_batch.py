@@ -131,3 +131,18 @@ def test_empty_and_invalid_batches(env):
     with pytest.raises(binding.DcoError) as e:
         st.match_batch([(L, L, 9, out)])   # D > W
     assert e.value.code == binding.DCO_EINVAL
+
+
+def test_handles_never_lower_each_others_kernel_limits(env):
+    # a wide pair needs more dynamic shared memory than a medium one; a second
+    # handle running the medium pair must not lower the first handle's limit
+    torch, binding, st = env
+    a, b = binding.Stereo(0), binding.Stereo(0)
+    wide = scenes.plane_scene(960, 96, 64, 4, seed=scenes.seed_for(3, 77), drange=(2, 60))
+    mid = scenes.plane_scene(400, 96, 32, 4, seed=scenes.seed_for(3, 78), drange=(2, 30))
+    r1 = a.match(_dev(torch, wide.left), _dev(torch, wide.right), wide.D).cpu().numpy()
+    b.match(_dev(torch, mid.left), _dev(torch, mid.right), mid.D)
+    r2 = a.match(_dev(torch, wide.left), _dev(torch, wide.right), wide.D).cpu().numpy()
+    assert np.array_equal(r1, r2)
+    a.close()
+    b.close()
