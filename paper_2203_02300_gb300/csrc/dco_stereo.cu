@@ -391,7 +391,8 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
 constexpr int kQS = 33;   // Q row stride: column d of consecutive rows hits distinct banks
 constexpr int kVSeg = 32; // rows per warp
 
-__host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)len * kQS + nw * 32 + 2 * len + nw; }
+// Q has one extra row of zeros in front (Q[-1], the prefix before the first row)
+__host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)(len + 1) * kQS + nw * 32 + 2 * len + nw; }
 
 __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz)
 {
@@ -402,7 +403,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     const int ys = bz * a.chunk, ye = min(H, ys + a.chunk);
     const int ya = max(0, ys - L1), yb = min(H, ye + L1);
     const int len = yb - ya;
-    uint32_t *Q = vsmem;                      // [len][kQS]
+    uint32_t *Q = vsmem + kQS;                // [len][kQS], Q[-1] = 0
     uint32_t *T = Q + len * kQS;              // [nw][32] segment sums
     uint32_t *NQ = T + nw * 32;               // [len] prefix of l + r + 1
     uint32_t *NT = NQ + len;                  // [nw]
@@ -431,6 +432,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     }
     const bool out_row = rin && ya + r >= ys && ya + r < ye;
     uint32_t bv = 0xffffffffu, bd = 0;
+    if (warp == 0) Q[-kQS + lane] = 0u;   // Q[-1]: read by rows whose up arm reaches the top
 
     for (int g = 0; g < ng; g++) {
         // ---- A: this warp's 32 rows of the slice column, lane = disparity
@@ -464,18 +466,29 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         if (out_row) {
             const int up = (aw >> 16) & 0xff, dn = aw >> 24;
             const uint32_t *qh = Q + (r + dn) * kQS;
-            const int lo = r - up - 1;
-            const uint32_t *ql = Q + max(lo, 0) * kQS;
-            const uint32_t lomask = lo >= 0 ? 0xffffffffu : 0u;
+            const int lo = r - up - 1;               // >= -1
+            const uint32_t *ql = Q + lo * kQS;
+            // running minimum; strict < keeps the smallest d on ties
+            uint32_t bj = 0xffffffffu, bmin = bv;
+            if (nlive == 32) {
 #pragma unroll 8
-            for (int j = 0; j < 32; j++) {
-                const uint32_t vv = qh[j] - (ql[j] & lomask);
-                if (j < nlive && vv < bv) { bv = vv; bd = (uint32_t)(dbase + j); }
+                for (int j = 0; j < 32; j++) {
+                    const uint32_t vv = qh[j] - ql[j];
+                    bj = vv < bmin ? (uint32_t)j : bj;
+                    bmin = min(bmin, vv);
+                }
+            } else {
+                for (int j = 0; j < nlive; j++) {
+                    const uint32_t vv = qh[j] - ql[j];
+                    bj = vv < bmin ? (uint32_t)j : bj;
+                    bmin = min(bmin, vv);
+                }
             }
+            if (bj != 0xffffffffu) { bv = bmin; bd = (uint32_t)dbase + bj; }
             if (want_vol) {
                 const uint32_t n = NQ[r + dn] - (lo >= 0 ? NQ[lo] : 0u);
                 for (int j = 0; j < nlive; j++) {
-                    const uint32_t vv = qh[j] - (ql[j] & lomask);
+                    const uint32_t vv = qh[j] - ql[j];
                     a.vol[((size_t)(dbase + j) * H + ya + r) * W + x] = float(vv) / (float(n) * a.S);
                 }
             }
