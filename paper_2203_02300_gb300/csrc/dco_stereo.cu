@@ -86,16 +86,32 @@ constexpr int kTX = 32, kTY = 8;
 constexpr int kMaxCW = 15, kMaxCH = 15;
 constexpr int kGW = 48;   // grey tile row pitch (>= kTX + kMaxCW - 1, multiple of 4)
 
-// any colour channel of |a - b| >= t, t4 = t replicated in four bytes (t <= 255)
-__device__ __forceinline__ bool any_ge(uint32_t a, uint32_t b, uint32_t t4)
+// Colour r | g<<8 | b<<16 spread into three 10-bit fields r | g<<10 | b<<20.
+// With K holding tau - 1 + 512 in every field, (E(c) + K - E(p)) keeps each
+// field in [1, 1023] (no carry or borrow between fields) and has the field's
+// bit 9 set exactly when c_i - p_i + tau - 1 >= 0; the same with c and p
+// swapped gives the other side, so every channel has |c_i - p_i| < tau
+// exactly when all six bit-9s are set.
+constexpr uint32_t kM9 = (1u << 9) | (1u << 19) | (1u << 29);
+__device__ __forceinline__ uint32_t spread10(uint32_t c)
 {
-    return (__vcmpgeu4(__vabsdiffu4(a, b), t4) & 0x00ffffffu) != 0u;
+    return (c & 0xffu) | ((c & 0xff00u) << 2) | ((c & 0xff0000u) << 4);
+}
+// all channels within tau of p, given Kp = K - E(p) and pK = E(p) + K
+__device__ __forceinline__ bool within(uint32_t ec, uint32_t Kp, uint32_t pK)
+{
+    return ((ec + Kp) & (pK - ec) & kM9) == kM9;
 }
 
-// 4 flags f_i = [byte_i(w) < c] -> bits f0 | f1<<1 | f2<<2 | f3<<3
-__device__ __forceinline__ uint32_t lt4(uint32_t w, uint32_t c4)
+// 4 flags f_i = [byte_i(w) < byte_i(c4)] -> bits f0 | f1<<1 | f2<<2 | f3<<3.
+// Per byte: (w|0x80) - (c&0x7f) never borrows into the next byte, and its top
+// bit is clear exactly when the low seven bits compare w < c; the top bits
+// of w and c decide the rest.
+__device__ __forceinline__ uint32_t lt4(uint32_t w, uint32_t c4, uint32_t c4lo)
 {
-    return (__vsetltu4(w, c4) * 0x01020408u) >> 24;
+    const uint32_t x = (w | 0x80808080u) - c4lo;
+    const uint32_t lt = ((~w & c4) | (~(w ^ c4) & ~x)) & 0x80808080u;
+    return (lt * 0x00204081u) >> 28;
 }
 
 template <int CW, int CH>
@@ -124,7 +140,7 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     const uint32_t yc = gs[ty + ry][tx + rx];
     unsigned long long bits = 0ull;
     if (CW == 9 && CH == 7) {
-        const uint32_t c4 = yc * 0x01010101u;
+        const uint32_t c4 = yc * 0x01010101u, c4lo = c4 & 0x7f7f7f7fu;
         const int al = tx & ~3, sh = 8 * (tx & 3);
         int k = 0;
 #pragma unroll
@@ -134,7 +150,7 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
             const uint32_t w0 = __funnelshift_r(a0, a1, sh);   // bytes dx 0..3
             const uint32_t w1 = __funnelshift_r(a1, a2, sh);   // bytes dx 4..7
             const uint32_t b8 = (__funnelshift_r(a2, 0u, sh) & 0xffu) < yc ? 1u : 0u;   // dx 8
-            const uint32_t f0 = lt4(w0, c4), f1 = lt4(w1, c4);
+            const uint32_t f0 = lt4(w0, c4, c4lo), f1 = lt4(w1, c4, c4lo);
             uint32_t rowbits;
             int nb;
             if (dy == 3) {   // centre row: dx 4 is the centre itself
@@ -164,8 +180,17 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     const int L1 = a.L1, L2 = a.L2;
     // a threshold >= 256 never stops an arm (channel differences are <= 255)
     const bool use1 = a.tau1 < 256, use2 = a.tau2 < 256;
-    const uint32_t t1 = 0x01010101u * (uint32_t)min(a.tau1, 255);
-    const uint32_t t2 = 0x01010101u * (uint32_t)min(a.tau2, 255);
+    const uint32_t k1 = 0x00100401u * (uint32_t)(min(a.tau1, 255) + 511);   // tau - 1 + 512 per field
+    const uint32_t k2 = 0x00100401u * (uint32_t)(min(a.tau2, 255) + 511);
+    const uint32_t ep = spread10(p);
+    const uint32_t K1p = k1 - ep, pK1 = ep + k1, K2p = k2 - ep, pK2 = ep + k2;
+    // step j fails: far from p or from its predecessor (tau1), or beyond L2
+    // and far from p (tau2)
+    auto fails = [&](uint32_t c, uint32_t prev, int j) -> bool {
+        const uint32_t ec = spread10(c), eq = spread10(prev);
+        if (use1 && (!within(ec, K1p, pK1) || !within(ec, k1 - eq, eq + k1))) return true;
+        return j > L2 && use2 && !within(ec, K2p, pK2);
+    };
     // the first kArmBatch candidates of all four directions are loaded at
     // once (in-image addresses only), so a typical pixel pays one load latency
     constexpr int kArmBatch = 2;
@@ -190,23 +215,17 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
 #pragma unroll
         for (int u = 0; u < kArmBatch; u++) {
             const int j = u + 1;
-            if (open && j <= lim[e]) {
-                const uint32_t c = cand[e][u];
-                if ((use1 && (any_ge(c, p, t1) || any_ge(c, prev, t1))) || (j > L2 && use2 && any_ge(c, p, t2)))
-                    open = false;
-                else {
-                    n = j;
-                    prev = c;
-                }
+            if (open && j <= lim[e] && !fails(cand[e][u], prev, j)) {
+                n = j;
+                prev = cand[e][u];
             } else {
                 open = false;
             }
         }
-        // rare long arms: continue one candidate at a time
+        // longer arms: continue one candidate at a time
         for (int j = kArmBatch + 1; open && j <= lim[e]; j++) {
             const uint32_t c = __ldg(rgbx + i + j * step[e]);
-            if ((use1 && (any_ge(c, p, t1) || any_ge(c, prev, t1))) || (j > L2 && use2 && any_ge(c, p, t2)))
-                break;
+            if (fails(c, prev, j)) break;
             n = j;
             prev = c;
         }
@@ -244,6 +263,11 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src)
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // byte offsets of the H block's shared-memory regions
@@ -254,7 +278,7 @@ struct HSmem {
         ref = kTabBytes;
         oth = ref + len * 16;
         arm = oth + (len + 32) * 16;
-        p = arm + (chunk + 3) / 4 * 16;
+        p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
         t = p + len * 128;
         total = t + nw * 128;
     }
@@ -273,10 +297,13 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     float *sTA = reinterpret_cast<float *>(smem_raw);
     float *sTC = sTA + kTabAD;
     uint4 *sref = reinterpret_cast<uint4 *>(smem_raw + L.ref);
-    uint4 *soth = reinterpret_cast<uint4 *>(smem_raw + L.oth);
+    // candidate records, split: census (8 bytes) and colour (4 bytes)
+    uint2 *socen = reinterpret_cast<uint2 *>(smem_raw + L.oth);
+    uint32_t *sorgb = reinterpret_cast<uint32_t *>(smem_raw + L.oth + (len + 32) * 8);
     uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);
-    uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32]
+    uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32], P[-1] = 0
     uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [nw][32]
+    if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
 
     // disparities of this group: [dlo, dhi] live
     const int dlo = a.d0 + 32 * g;
@@ -292,7 +319,10 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     for (int i = threadIdx.x; i < kTabBytes / 16; i += blockDim.x)
         cp_async16(smem_raw + 16 * i, reinterpret_cast<const uint8_t *>(a.tables) + 16 * i);
     for (int i = threadIdx.x; i < len; i += blockDim.x) cp_async16(sref + i, rref + xa + i);
-    for (int i = threadIdx.x; i < olen; i += blockDim.x) cp_async16(soth + i, roth + olo + i);
+    for (int i = threadIdx.x; i < olen; i += blockDim.x) {
+        cp_async8(socen + i, &roth[olo + i].x);   // census words
+        cp_async4(sorgb + i, &roth[olo + i].z);   // colour and Lmin
+    }
     for (int i = threadIdx.x; i < xe - xs; i += blockDim.x) cp_async4(sarm + i, aref + xs + i);
     cp_async_wait_all();
     __syncthreads();
@@ -321,7 +351,8 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
 #pragma unroll
         for (int u = 0; u < kHU; u++) {
             pr[u] = sref[x0 + u];
-            po[u] = soth[x0 + u + xa + oi];
+            const uint2 c = socen[x0 + u + xa + oi];
+            po[u] = make_uint4(c.x, c.y, sorgb[x0 + u + xa + oi], 0u);
         }
         uint32_t c[kHU];
 #pragma unroll
@@ -333,7 +364,8 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
         }
     }
     for (; x0 < sb; x0++) {
-        run += cost_at(sref[x0], soth[x0 + xa + oi], x0);
+        const uint2 c = socen[x0 + xa + oi];
+        run += cost_at(sref[x0], make_uint4(c.x, c.y, sorgb[x0 + xa + oi], 0u), x0);
         P[x0 * 32 + lane] = run;
     }
     T[warp * 32 + lane] = run;
@@ -362,15 +394,15 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
         const uchar4 am0 = sarm[i], am1 = sarm[i + nw];
         const int hi0 = base + i + am0.y, lo0 = base + i - am0.x - 1;   // lo >= -1
         const int hi1 = base + i + nw + am1.y, lo1 = base + i + nw - am1.x - 1;
-        const uint32_t v0 = Pl[hi0 * 32] - (lo0 >= 0 ? Pl[lo0 * 32] : 0u);
-        const uint32_t v1 = Pl[hi1 * 32] - (lo1 >= 0 ? Pl[lo1 * 32] : 0u);
+        const uint32_t v0 = Pl[hi0 * 32] - Pl[lo0 * 32];
+        const uint32_t v1 = Pl[hi1 * 32] - Pl[lo1 * 32];
         o[0] = v0;
         o[ostep] = v1;
     }
     if (i < n_out) {
         const uchar4 am = sarm[i];
         const int hi = base + i + am.y, lo = base + i - am.x - 1;
-        *o = Pl[hi * 32] - (lo >= 0 ? Pl[lo * 32] : 0u);
+        *o = Pl[hi * 32] - Pl[lo * 32];
     }
 }
 
@@ -413,6 +445,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     const uint32_t *arms = reinterpret_cast<const uint32_t *>(view ? a.arms[1] : a.arms[0]) + x;
     const size_t rowstride = (size_t)W * a.dstride;
     const int sa = warp * kVSeg, sb = min(len, sa + kVSeg);   // relative to ya
+    const bool full = sb - sa == kVSeg;
     const int ng = (a.dc + 31) / 32;
     const bool want_vol = a.vol != nullptr && view == a.vol_view;
 
@@ -436,10 +469,20 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
 
     for (int g = 0; g < ng; g++) {
         // ---- A: this warp's 32 rows of the slice column, lane = disparity
+        // one 64-bit base per group, 32-bit row offsets (31 * W * dstride
+        // < 2^32 for W <= 16384, D <= 256); full segments need no predicates
         uint32_t v[kVSeg];
         const uint32_t *src = sh + (size_t)(ya + sa) * rowstride + g * 32;
+        const uint32_t rs = (uint32_t)rowstride;
+        if (full) {
+            uint32_t off = 0;
 #pragma unroll
-        for (int u = 0; u < kVSeg; u++) v[u] = sa + u < sb ? __ldg(src + (size_t)u * rowstride) : 0u;
+            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = __ldg(src + off);
+        } else {
+            uint32_t off = 0;
+#pragma unroll
+            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = sa + u < sb ? __ldg(src + off) : 0u;
+        }
         uint32_t tot = 0;
 #pragma unroll
         for (int u = 0; u < kVSeg; u++) tot += v[u];
@@ -454,10 +497,18 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             if (rin) NQ[r] += noff;
         }
         uint32_t *q = Q + sa * kQS + lane;
+        if (full) {
 #pragma unroll
-        for (int u = 0; u < kVSeg; u++) {
-            run += v[u];
-            if (sa + u < sb) q[u * kQS] = run;
+            for (int u = 0; u < kVSeg; u++) {
+                run += v[u];
+                q[u * kQS] = run;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kVSeg; u++) {
+                run += v[u];
+                if (sa + u < sb) q[u * kQS] = run;
+            }
         }
         __syncthreads();
         // ---- C: lane = output row, loop over the group's disparities
@@ -859,12 +910,12 @@ dco_status ensure_ws(dco_stereo *h, size_t need)
     return DCO_OK;
 }
 
-dco_status ensure_tables(dco_stereo *h, const dco_params &p, const Derived &dv, cudaStream_t s)
+// Eq. 1 tables, evaluated in double on the host and rounded once to float:
+//   [0, kTabAD)   1 - exp(-(k/3) / lambda_AD), k = 0..765 (the channel sum);
+//   [kTabAD, +kTabCen)   1 - exp(-h / lambda_census), h = 0..64;
+//   [kTabAD + kTabCen, +kTabAlpha)   alpha(Lmin) * S.
+void fill_tables(float *t, const dco_params &p, const Derived &dv)
 {
-    const float key[4] = {p.lambda_ad, p.lambda_census, p.gamma_l, p.eps};
-    if (h->tab_valid && !std::memcmp(key, h->tab_key, sizeof key) && h->tab_l1 == p.arm_l1) return DCO_OK;
-    float *t = h->h_tables;
-    // Eq. 1 terms, evaluated in double on the host and rounded once to float
     for (int k = 0; k < kTabAD; k++)
         t[k] = k <= 765 ? (float)(1.0 - std::exp(-(k / 3.0) / (double)p.lambda_ad)) : 1.0f;
     for (int k = 0; k < kTabCen; k++)
@@ -873,6 +924,14 @@ dco_status ensure_tables(dco_stereo *h, const dco_params &p, const Derived &dv, 
         const double alpha = 1.0 - std::exp(-(double)p.gamma_l / ((double)l + (double)p.eps));
         t[kTabAD + kTabCen + l] = (float)(alpha * (double)dv.Sint);
     }
+}
+
+dco_status ensure_tables(dco_stereo *h, const dco_params &p, const Derived &dv, cudaStream_t s)
+{
+    const float key[4] = {p.lambda_ad, p.lambda_census, p.gamma_l, p.eps};
+    if (h->tab_valid && !std::memcmp(key, h->tab_key, sizeof key) && h->tab_l1 == p.arm_l1) return DCO_OK;
+    float *t = h->h_tables;
+    fill_tables(t, p, dv);
     DCO_CUDA(h, cudaMemcpyAsync(h->d_tables, t, sizeof(float) * kTabFloats, cudaMemcpyHostToDevice, s));
     // the pinned staging buffer is reused by the next upload: wait for this one
     DCO_CUDA(h, cudaStreamSynchronize(s));
@@ -1506,14 +1565,7 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
 
     // Eq. 1 tables (host double, rounded once to float) into the scratch
     float tab[kTabFloats];
-    for (int k = 0; k < kTabAD; k++)
-        tab[k] = k <= 765 ? (float)(1.0 - std::exp(-(k / 3.0) / (double)p.lambda_ad)) : 1.0f;
-    for (int k = 0; k < kTabCen; k++)
-        tab[kTabAD + k] = k <= 64 ? (float)(1.0 - std::exp(-(double)k / (double)p.lambda_census)) : 1.0f;
-    for (int l = 0; l < kTabAlpha; l++) {
-        const double alpha = 1.0 - std::exp(-(double)p.gamma_l / ((double)l + (double)p.eps));
-        tab[kTabAD + kTabCen + l] = (float)(alpha * (double)dv.Sint);
-    }
+    fill_tables(tab, p, dv);
     if (cudaMemcpyAsync(base, tab, sizeof tab, cudaMemcpyHostToDevice, s) != cudaSuccess) return DCO_ECUDA;
 
     // a handle that owns nothing: its workspace and tables are the scratch
