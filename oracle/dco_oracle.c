@@ -31,6 +31,12 @@
  *   - WTA (Eq. 3) takes the smallest d among equal minima.
  *   - outlier removal: left-right consistency, valid iff x - dL >= 0 and
  *     |dL(x) - dR(x - dL)| <= tol, otherwise -1.
+ *   - parallax optimisation (Sect. 4.3, Eq. 4), applied to the checked map:
+ *     every valid pixel p takes the disparity that occurs most often among
+ *     the valid pixels of its support region N_p (the same region as Eq. 2,
+ *     left-view arms), the smallest such d on equal counts; invalid pixels
+ *     cast no vote and stay invalid.  k iterations each read the whole map
+ *     of the previous one.
  */
 #include <math.h>
 #include <stdint.h>
@@ -309,5 +315,54 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
     }
 done:
     free(cl); free(cr); free(al); free(ar);
+    return rc;
+}
+
+/*
+ * Parallax optimisation (Sect. 4.3, Eq. 4): `iters` rounds of
+ *   d'(p) = argmax_d hist(d, N_p)
+ * on a W x H map with disparities in [0, D-1] (-1 = invalid), N_p being the
+ * support region of Eq. 2 built from `arms` (4 bytes per pixel: l, r, u, d).
+ * The histogram counts every pixel of the region explicitly (pixels of the
+ * region are enumerated row by row; the region is a union of disjoint row
+ * segments, so no pixel is counted twice).
+ */
+int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int iters, int16_t *out)
+{
+    if (!disp || !arms || !out || W < 1 || H < 1 || D < 1 || iters < 0) return ORC_EINVAL;
+    long n = (long)W * H;
+    int16_t *cur = (int16_t *)malloc(sizeof(int16_t) * n);
+    int16_t *nxt = (int16_t *)malloc(sizeof(int16_t) * n);
+    if (!cur || !nxt) { free(cur); free(nxt); return ORC_ENOMEM; }
+    memcpy(cur, disp, sizeof(int16_t) * n);
+    int rc = ORC_OK;
+    for (int it = 0; it < iters && rc == ORC_OK; it++) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int y = 0; y < H; y++) {
+            long *hist = (long *)malloc(sizeof(long) * D);
+            if (!hist) { rc = ORC_ENOMEM; continue; }
+            for (int x = 0; x < W; x++) {
+                long i = (long)y * W + x;
+                if (cur[i] < 0) { nxt[i] = -1; continue; }
+                for (int d = 0; d < D; d++) hist[d] = 0;
+                const uint8_t *ap = arms + 4 * i;
+                for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {
+                    const uint8_t *aq = arms + 4 * ((long)yy * W + x);
+                    for (int xx = x - aq[0]; xx <= x + aq[1]; xx++) {
+                        int v = cur[(long)yy * W + xx];
+                        if (v >= 0 && v < D) hist[v]++;
+                    }
+                }
+                int best = 0;
+                for (int d = 1; d < D; d++)
+                    if (hist[d] > hist[best]) best = d;   /* strict: smallest d on ties */
+                nxt[i] = (int16_t)best;
+            }
+            free(hist);
+        }
+        int16_t *t = cur; cur = nxt; nxt = t;
+    }
+    if (rc == ORC_OK) memcpy(out, cur, sizeof(int16_t) * n);
+    free(cur); free(nxt);
     return rc;
 }

@@ -42,6 +42,8 @@ def lib():
         L.orc_cost_terms.restype = d
         L.orc_lr_check.argtypes = [P, P, i, i, i, P]
         L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i] + [P] * 9
+        L.orc_vote.argtypes = [P, P, i, i, i, i, P]
+        L.orc_vote.restype = i
         L.orc_grey.restype = i
         L.orc_census.restype = i
         L.orc_hamming.restype = i
@@ -127,6 +129,19 @@ def lr_check(dl: np.ndarray, dr: np.ndarray, tol: int = 1) -> np.ndarray:
     rows, W = dl.shape
     out = np.empty_like(dl)
     _check(lib().orc_lr_check(_ptr(dl), _ptr(dr), W, rows, tol, _ptr(out)))
+    return out
+
+
+def vote(disp: np.ndarray, arm: np.ndarray, D: int, iters: int = 1) -> np.ndarray:
+    """Parallax optimisation (Sect. 4.3, Eq. 4): `iters` rounds of the mode of
+    the valid disparities over each valid pixel's support region (arms of
+    the reference view, (H, W, 4) uint8 l, r, u, d)."""
+    disp = np.ascontiguousarray(disp, np.int16)
+    arm = np.ascontiguousarray(arm, np.uint8)
+    H, W = disp.shape
+    assert arm.shape == (H, W, 4)
+    out = np.empty_like(disp)
+    _check(lib().orc_vote(_ptr(disp), _ptr(arm), W, H, D, iters, _ptr(out)))
     return out
 
 

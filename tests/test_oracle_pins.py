@@ -400,3 +400,112 @@ def test_arms_brute_force_with_strong_noise():
         for x in range(img.shape[1]):
             for e, (ex, ey) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
                 assert a[y, x, e] == brute_arm(img, x, y, ex, ey, p), (y, x, e)
+
+
+# ----------------------------------------------------------------- Eq. 4 vote
+def full_arms(H, W):
+    """Arms reaching the image border in every direction: N_p = whole image."""
+    a = np.zeros((H, W, 4), np.uint8)
+    ys, xs = np.mgrid[0:H, 0:W]
+    a[..., 0], a[..., 1], a[..., 2], a[..., 3] = xs, W - 1 - xs, ys, H - 1 - ys
+    return a
+
+
+def random_arms(rng, H, W, reach=3):
+    """Arms within the image, at most `reach` long."""
+    ys, xs = np.mgrid[0:H, 0:W]
+    a = np.zeros((H, W, 4), np.uint8)
+    for k, room in enumerate((xs, W - 1 - xs, ys, H - 1 - ys)):
+        a[..., k] = np.minimum(room, rng.integers(0, reach + 1, (H, W)))
+    return a
+
+
+def vote_bruteforce(disp, arm, D, iters):
+    """Eq. 4 written from the definition: the region as a set of coordinates
+    (union over q on p's vertical arm of q's horizontal segment), a Python
+    dictionary of counts, max count with the smallest d."""
+    H, W = disp.shape
+    cur = disp.astype(int).copy()
+    for _ in range(iters):
+        nxt = cur.copy()
+        for y in range(H):
+            for x in range(W):
+                if cur[y, x] < 0:
+                    continue
+                region = set()
+                for yy in range(y - int(arm[y, x, 2]), y + int(arm[y, x, 3]) + 1):
+                    l, r = int(arm[yy, x, 0]), int(arm[yy, x, 1])
+                    region.update((xx, yy) for xx in range(x - l, x + r + 1))
+                counts = {}
+                for (xx, yy) in region:
+                    v = cur[yy, xx]
+                    if 0 <= v < D:
+                        counts[v] = counts.get(v, 0) + 1
+                top = max(counts.values())
+                nxt[y, x] = min(v for v, c in counts.items() if c == top)
+        cur = nxt
+    return cur.astype(np.int16)
+
+
+def test_vote_constant_map_is_a_fixed_point():
+    s = scenes.plane_scene(40, 30, 16, 3, seed=11, drange=(1, 14))
+    arm = O.arms(s.left)
+    d = np.full((30, 40), 7, np.int16)
+    d[::5, ::3] = -1
+    for k in (1, 3):
+        out = O.vote(d, arm, 16, k)
+        assert np.array_equal(out, d)
+
+
+def test_vote_replaces_an_isolated_outlier():
+    d = np.full((9, 9), 4, np.int16)
+    d[4, 4] = 9
+    out = O.vote(d, full_arms(9, 9), 12, 1)
+    assert (out == 4).all()
+
+
+def test_vote_tie_takes_the_smallest_disparity():
+    # two pixels joined by their arms, one vote each
+    d = np.array([[5, 3]], np.int16)
+    a = np.array([[[0, 1, 0, 0], [1, 0, 0, 0]]], np.uint8)
+    assert O.vote(d, a, 8, 1).tolist() == [[3, 3]]
+
+
+def test_vote_invalid_pixels_neither_vote_nor_change():
+    d = np.array([[-1, -1, 2, -1, 7]], np.int16)
+    out = O.vote(d, full_arms(1, 5), 8, 1)
+    assert out.tolist() == [[-1, -1, 2, -1, 2]]   # {2: 1, 7: 1}: tie -> 2
+    d2 = np.array([[-1, 6, -1]], np.int16)
+    assert O.vote(d2, full_arms(1, 3), 8, 2).tolist() == [[-1, 6, -1]]
+
+
+def test_vote_region_is_h_then_v():
+    # p's vertical arm reaches row 0, whose horizontal arm reaches x = 0;
+    # row 1's horizontal arm is empty, so x = 0 of row 1 is not in N_p
+    d = np.array([[3, 5], [3, 5]], np.int16)
+    a = np.zeros((2, 2, 4), np.uint8)
+    a[1, 1, 2] = 1         # (1, 1): up arm 1
+    a[0, 1, 0] = 1         # (0, 1): left arm 1
+    out = O.vote(d, a, 8, 1)
+    # N_(1,1) = {(1,1), (1,0), (0,0)} in (x, y): votes 5, 5, 3 -> 5
+    assert out[1, 1] == 5
+    a[1, 1, 0] = 1         # now row 1 also reaches x = 0: votes 5, 3, 5, 3 -> tie -> 3
+    assert O.vote(d, a, 8, 1)[1, 1] == 3
+
+
+def test_vote_matches_bruteforce():
+    rng = np.random.default_rng(4)
+    for H, W, D in ((5, 7, 6), (8, 6, 4), (1, 9, 5)):
+        d = rng.integers(-1, D, (H, W)).astype(np.int16)
+        a = random_arms(rng, H, W)
+        for k in (1, 2, 3):
+            assert np.array_equal(O.vote(d, a, D, k), vote_bruteforce(d, a, D, k)), (H, W, D, k)
+
+
+def test_vote_iterations_compose():
+    rng = np.random.default_rng(5)
+    d = rng.integers(-1, 12, (20, 24)).astype(np.int16)
+    a = random_arms(rng, 20, 24, reach=5)
+    once = O.vote(d, a, 12, 1)
+    assert np.array_equal(O.vote(d, a, 12, 2), O.vote(once, a, 12, 1))
+    assert np.array_equal(O.vote(d, a, 12, 0), d)
