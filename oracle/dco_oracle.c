@@ -35,7 +35,8 @@
  *     every valid pixel p takes the disparity that occurs most often among
  *     the valid pixels of its support region N_p (the same region as Eq. 2,
  *     left-view arms), the smallest such d on equal counts; invalid pixels
- *     cast no vote and stay invalid.  k iterations each read the whole map
+ *     (any value outside [0, D-1], -1 after the check) cast no vote and are
+ *     written as -1.  k iterations each read the whole map
  *     of the previous one.
  */
 #include <math.h>
@@ -343,7 +344,7 @@ int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int 
             if (!hist) { rc = ORC_ENOMEM; continue; }
             for (int x = 0; x < W; x++) {
                 long i = (long)y * W + x;
-                if (cur[i] < 0) { nxt[i] = -1; continue; }
+                if (cur[i] < 0 || cur[i] >= D) { nxt[i] = -1; continue; }   /* invalid */
                 for (int d = 0; d < D; d++) hist[d] = 0;
                 const uint8_t *ap = arms + 4 * i;
                 for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {

@@ -430,7 +430,8 @@ def vote_bruteforce(disp, arm, D, iters):
         nxt = cur.copy()
         for y in range(H):
             for x in range(W):
-                if cur[y, x] < 0:
+                if not 0 <= cur[y, x] < D:
+                    nxt[y, x] = -1
                     continue
                 region = set()
                 for yy in range(y - int(arm[y, x, 2]), y + int(arm[y, x, 3]) + 1):
@@ -477,6 +478,9 @@ def test_vote_invalid_pixels_neither_vote_nor_change():
     assert out.tolist() == [[-1, -1, 2, -1, 2]]   # {2: 1, 7: 1}: tie -> 2
     d2 = np.array([[-1, 6, -1]], np.int16)
     assert O.vote(d2, full_arms(1, 3), 8, 2).tolist() == [[-1, 6, -1]]
+    # values beyond the range are invalid too: no vote, written as -1
+    d3 = np.array([[9, 4, 4, 12]], np.int16)
+    assert O.vote(d3, full_arms(1, 4), 8, 1).tolist() == [[-1, 4, 4, -1]]
 
 
 def test_vote_region_is_h_then_v():
@@ -496,7 +500,7 @@ def test_vote_region_is_h_then_v():
 def test_vote_matches_bruteforce():
     rng = np.random.default_rng(4)
     for H, W, D in ((5, 7, 6), (8, 6, 4), (1, 9, 5)):
-        d = rng.integers(-1, D, (H, W)).astype(np.int16)
+        d = rng.integers(-1, D + 1, (H, W)).astype(np.int16)   # D: out of range
         a = random_arms(rng, H, W)
         for k in (1, 2, 3):
             assert np.array_equal(O.vote(d, a, D, k), vote_bruteforce(d, a, D, k)), (H, W, D, k)
