@@ -68,7 +68,9 @@ typedef enum {
  *   direction is the largest k <= arm_l1 such that every step j <= k stays in
  *   the image, has max-channel difference < tau1 to p and to step j-1, and,
  *   when j > arm_l2, < tau2 to p (defaults 34, 17, 20, 6);
- *   lr_tol = 1 (a negative value disables the consistency check).
+ *   lr_tol = 1 (a negative value disables the consistency check);
+ *   vote_iters = 0: rounds of the parallax optimisation of Sect. 4.3 (Eq. 4)
+ *   applied to the checked map (see dco_stereo_vote), 0..64.
  */
 typedef struct {
     float lambda_ad;
@@ -83,6 +85,7 @@ typedef struct {
     int tau2;
     int lr_tol;
     int d_chunk; /* disparities aggregated per pass (0 = automatic); see dco_stereo_match */
+    int vote_iters; /* Eq. 4 rounds after the consistency check (0 = none) */
 } dco_params;
 
 /* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */
@@ -121,7 +124,8 @@ dco_status dco_stereo_reserve(dco_stereo *h, int W, int H, int D, const dco_para
  * The whole hot path for one rectified pair (Sect. 4.1-4.3):
  *   census + grey + arms for both views -> Eq. 1 costs -> Eq. 2 horizontal
  *   then vertical aggregation over the cross-support region -> Eq. 3 WTA
- *   for the left- and right-reference views -> left-right check.
+ *   for the left- and right-reference views -> left-right check ->
+ *   p->vote_iters rounds of the Eq. 4 parallax optimisation (left view).
  * left, right: device, W*H*3 bytes.  disp_out: device, W*H int16.
  * The disparity range is processed in passes of p->d_chunk disparities
  * (automatic when 0) so the workspace holds slices, never the volume.
@@ -177,6 +181,19 @@ dco_status dco_stereo_arms(dco_stereo *h, const uint8_t *rgb, int W, int H,
 dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint8_t *right,
                                   int W, int H, int D, const dco_params *p, int view,
                                   float *vol_out, dco_stream stream);
+
+/*
+ * Parallax optimisation alone (Sect. 4.3, Eq. 4), p->vote_iters rounds:
+ *   d'(p) = argmax_d hist(d, N_p)
+ * over the valid pixels of the support region N_p of Eq. 2 (the arms of
+ * `rgb`, the reference image, under p's arm parameters); the smallest d on
+ * equal counts.  Pixels of disp_in outside [0, D-1] (-1 = invalid) cast no
+ * vote and are written as -1.  Each round reads the whole previous map.
+ * rgb: device W*H*3 bytes; disp_in, disp_out: device W*H int16 (may be the
+ * same buffer).  0 rounds copies the map.  Same errors as dco_stereo_match.
+ */
+dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *disp_in, int W, int H, int D,
+                           const dco_params *p, int16_t *disp_out, dco_stream stream);
 
 /*
  * Stage a7 alone: left-right consistency.  out(x,y) = dl(x,y) if

@@ -30,7 +30,7 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_ad", c_float), ("lambda_census", c_float), ("gamma_l", c_float),
                 ("eps", c_float), ("census_w", c_int), ("census_h", c_int), ("arm_l1", c_int),
                 ("arm_l2", c_int), ("tau1", c_int), ("tau2", c_int), ("lr_tol", c_int),
-                ("d_chunk", c_int)]
+                ("d_chunk", c_int), ("vote_iters", c_int)]
 
     @classmethod
     def default(cls, **over) -> "Params":
@@ -84,6 +84,7 @@ def lib():
             "dco_stereo_arms": (c_int, [P, P, c_int, c_int, P, P, P]),
             "dco_stereo_cost_volume": (c_int, [P, P, P, c_int, c_int, c_int, P, c_int, P, P]),
             "dco_stereo_lr_check": (c_int, [P, P, P, c_int, c_int, c_int, P, P]),
+            "dco_stereo_vote": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P]),
             "dco_stereo_match_batch": (c_int, [P, P, c_int, P, P]),
             "dco_stereo_sync_status": (c_int, [P]),
             "dco_stereo_last_error": (ctypes.c_char_p, [P]),
@@ -248,6 +249,19 @@ class Stereo:
         out = torch.empty_like(dl)
         _check(lib().dco_stereo_lr_check(self._h, _ptr(dl), _ptr(dr), W, H, tol, _ptr(out),
                                          _stream(stream)), self._h)
+        return out
+
+    def vote(self, img, disp, D: int, params: Optional[Params] = None, out=None, stream=None):
+        """params.vote_iters rounds of the Eq. 4 parallax optimisation of the
+        int16 map `disp` over the support regions of `img` (device tensors)."""
+        import torch
+        W, H = _rgb_dims(img)
+        assert tuple(disp.shape) == (H, W) and disp.dtype == torch.int16
+        if out is None:
+            out = torch.empty_like(disp)
+        _check(lib().dco_stereo_vote(self._h, _ptr(img), _ptr(disp), W, H, D,
+                                     ctypes.byref(params) if params else None, _ptr(out), _stream(stream)),
+               self._h)
         return out
 
     # -- status and profiling

@@ -284,6 +284,50 @@ struct HSmem {
     }
 };
 
+// Phases B and C of a horizontal pass (cost or vote).  P holds every warp's
+// local inclusive prefix of its segment [sa, sb) (relative to the prefix
+// range), T the segment totals (visible after a barrier).
+//   B. exclusive segment offsets, added to P in place;
+//   C. every output column c (n_out of them, prefix index base + c):
+//      S_H = P(c + r) - P(c - l - 1), written to o + c * ds (the horizontal
+//      part of Eq. 2).  Unsigned wrap-around makes the differences exact.
+__device__ __forceinline__ void hagg_tail(uint32_t *P, const uint32_t *T, const uchar4 *sarm, int sa, int sb,
+                                          int n_out, int base, uint32_t *o, size_t ds)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    uint32_t offs = 0;
+    for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
+    if (warp > 0) {
+        uint32_t *q = P + sa * 32 + lane;
+        int x = sa;
+        for (; x + 8 <= sb; x += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) q[u * 32] += offs;
+            q += 256;
+        }
+        for (; x < sb; x++, q += 32) *q += offs;
+    }
+    __syncthreads();
+    const size_t ostep = (size_t)nw * ds;
+    o += warp * ds;
+    const uint32_t *Pl = P + lane;
+    int i = warp;
+    for (; i + nw < n_out; i += 2 * nw, o += 2 * ostep) {
+        const uchar4 am0 = sarm[i], am1 = sarm[i + nw];
+        const int hi0 = base + i + am0.y, lo0 = base + i - am0.x - 1;   // lo >= -1
+        const int hi1 = base + i + nw + am1.y, lo1 = base + i + nw - am1.x - 1;
+        const uint32_t v0 = Pl[hi0 * 32] - Pl[lo0 * 32];
+        const uint32_t v1 = Pl[hi1 * 32] - Pl[lo1 * 32];
+        o[0] = v0;
+        o[ostep] = v1;
+    }
+    if (i < n_out) {
+        const uchar4 am = sarm[i];
+        const int hi = base + i + am.y, lo = base + i - am.x - 1;
+        *o = Pl[hi * 32] - Pl[lo * 32];
+    }
+}
+
 __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -370,40 +414,60 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     }
     T[warp * 32 + lane] = run;
     __syncthreads();
-    // ---- B: exclusive segment offsets, added in place
-    uint32_t offs = 0;
-    for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
-    if (warp > 0) {
-        uint32_t *q = P + sa * 32 + lane;
-        int x = sa;
-        for (; x + 8 <= sb; x += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; u++) q[u * 32] += offs;
-            q += 256;
-        }
-        for (; x < sb; x++, q += 32) *q += offs;
+    hagg_tail(P, T, sarm, sa, sb, xe - xs, xs - xa,
+              (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32 + lane, a.dstride);
+}
+
+// ---------------------------------------------------------------- k_hvote
+// Horizontal pass of the parallax optimisation (Sect. 4.3, Eq. 4): the same
+// block layout and phases as k_hagg, with the cost replaced by the indicator
+// [disp(x, y) == d] of the map being voted on (-1 matches no d), so S_H holds
+// the number of pixels of each horizontal segment that vote for d.
+struct HVSmem {
+    int disp, arm, p, t, total;
+    __host__ __device__ HVSmem(int len, int chunk, int nw)
+    {
+        disp = 0;
+        arm = (len * 2 + 15) / 16 * 16;
+        p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
+        t = p + len * 128;
+        total = t + nw * 128;
     }
+};
+
+__device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int bz)
+{
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int W = a.W, L1 = a.L1;
+    const int y = by, g = bz;
+    const int xs = bx * a.chunk, xe = min(W, xs + a.chunk);
+    const int xa = max(0, xs - L1), xb = min(W, xe + L1), len = xb - xa;
+    const HVSmem L(len, a.chunk, nw);
+    int16_t *sd = reinterpret_cast<int16_t *>(smem_raw + L.disp);
+    uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);
+    uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32], P[-1] = 0
+    uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [nw][32]
+    if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
+    const int16_t *drow = a.disp + (size_t)y * W;
+    const uchar4 *aref = a.arms + (size_t)y * W;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) sd[i] = drow[xa + i];
+    for (int i = threadIdx.x; i < xe - xs; i += blockDim.x) sarm[i] = aref[xs + i];
     __syncthreads();
-    // ---- C: horizontal segment sums of the output columns
-    const int n_out = xe - xs, base = xs - xa;
-    const size_t ostep = (size_t)nw * a.dstride;
-    uint32_t *o = (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs + warp) * a.dstride + g * 32 + lane;
-    const uint32_t *Pl = P + lane;
-    int i = warp;
-    for (; i + nw < n_out; i += 2 * nw, o += 2 * ostep) {
-        const uchar4 am0 = sarm[i], am1 = sarm[i + nw];
-        const int hi0 = base + i + am0.y, lo0 = base + i - am0.x - 1;   // lo >= -1
-        const int hi1 = base + i + nw + am1.y, lo1 = base + i + nw - am1.x - 1;
-        const uint32_t v0 = Pl[hi0 * 32] - Pl[lo0 * 32];
-        const uint32_t v1 = Pl[hi1 * 32] - Pl[lo1 * 32];
-        o[0] = v0;
-        o[ostep] = v1;
+
+    // ---- A: votes and local prefix of this warp's segment (lane = d)
+    const int d = a.d0 + 32 * g + lane;
+    const int sa = warp * kHSeg, sb = min(len, sa + kHSeg);   // relative to xa
+    uint32_t run = 0;
+#pragma unroll 8
+    for (int x = sa; x < sb; x++) {
+        run += sd[x] == d ? 1u : 0u;
+        P[x * 32 + lane] = run;
     }
-    if (i < n_out) {
-        const uchar4 am = sarm[i];
-        const int hi = base + i + am.y, lo = base + i - am.x - 1;
-        *o = Pl[hi * 32] - Pl[lo * 32];
-    }
+    T[warp * 32 + lane] = run;
+    __syncthreads();
+    hagg_tail(P, T, sarm, sa, sb, xe - xs, xs - xa, a.sh + ((size_t)y * W + xs) * a.dstride + g * 32 + lane,
+              a.dstride);
 }
 
 // ------------------------------------------------------------------ k_vagg
@@ -426,6 +490,10 @@ constexpr int kVSeg = 32; // rows per warp
 // Q has one extra row of zeros in front (Q[-1], the prefix before the first row)
 __host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)(len + 1) * kQS + nw * 32 + 2 * len + nw; }
 
+// kMax: the WTA takes the largest V (the vote counts of Eq. 4) instead of the
+// smallest: V is complemented, so the strict < keeps the smallest d on ties
+// and the key merge across passes is unchanged
+template <bool kMax>
 __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint32_t vsmem[];
@@ -524,13 +592,13 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             if (nlive == 32) {
 #pragma unroll 8
                 for (int j = 0; j < 32; j++) {
-                    const uint32_t vv = qh[j] - ql[j];
+                    const uint32_t vv = kMax ? ~(qh[j] - ql[j]) : qh[j] - ql[j];
                     bj = vv < bmin ? (uint32_t)j : bj;
                     bmin = min(bmin, vv);
                 }
             } else {
                 for (int j = 0; j < nlive; j++) {
-                    const uint32_t vv = qh[j] - ql[j];
+                    const uint32_t vv = kMax ? ~(qh[j] - ql[j]) : qh[j] - ql[j];
                     bj = vv < bmin ? (uint32_t)j : bj;
                     bmin = min(bmin, vv);
                 }
@@ -558,7 +626,8 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         key = prev <= key ? prev : key;   // earlier passes hold smaller d
     }
     if (a.last) {
-        disp[i] = (int16_t)(key & 0xffffffffu);
+        const bool invalid = kMax && (a.mask[i] < 0 || a.mask[i] >= a.D);   // Eq. 4: no vote, stays invalid
+        disp[i] = invalid ? (int16_t)-1 : (int16_t)(key & 0xffffffffu);
         if (cost) {
             const int up = (aw >> 16) & 0xff, dn = aw >> 24;
             const int lo = r - up - 1;
@@ -638,12 +707,20 @@ __global__ void __launch_bounds__(16 * 32) k_hagg(const __grid_constant__ Batch<
     hagg_body(b.p[i], bx, by, bz);
 }
 
-template <int N>
+template <int N, bool kMax>
 __global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
 {
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
-    vagg_body(b.p[i], bx, by, bz);
+    vagg_body<kMax>(b.p[i], bx, by, bz);
+}
+
+template <int N>
+__global__ void __launch_bounds__(16 * 32) k_hvote(const __grid_constant__ Batch<HVArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    hvote_body(b.p[i], bx, by, bz);
 }
 
 template <int N>
@@ -688,7 +765,7 @@ struct Derived {
 };
 
 struct Layout {
-    size_t rgbx[2], grey[2], rec[2], arms[2], best[2], disp[2], sh[2], total;
+    size_t rgbx[2], grey[2], rec[2], arms[2], best[2], disp[2], sh[2], vtmp, total;
     int dc, dstride, npass, rpitch;
 };
 
@@ -716,6 +793,7 @@ bool params_valid(const dco_params &p)
     if (p.census_w > kMaxCW || p.census_h > kMaxCH || p.census_w * p.census_h - 1 > 64) return false;
     if (p.arm_l1 < 1 || p.arm_l1 > kMaxL1 || p.arm_l2 < 0 || p.tau1 < 0 || p.tau2 < 0) return false;
     if (p.d_chunk < 0) return false;
+    if (p.vote_iters < 0 || p.vote_iters > 64) return false;
     return true;
 }
 
@@ -753,6 +831,8 @@ Layout make_layout(int W, int H, int D, const dco_params &p, int dc_override = 0
     for (int v = 0; v < 2; v++) { L.best[v] = off; off = align_up(off + (L.npass > 1 ? 8 * npx : 0)); }
     for (int v = 0; v < 2; v++) { L.disp[v] = off; off = align_up(off + 2 * npx); }
     for (int v = 0; v < 2; v++) { L.sh[v] = off; off = align_up(off + 4 * npx * (size_t)L.dstride); }
+    L.vtmp = off;   // second map of the Eq. 4 rounds
+    off = align_up(off + (p.vote_iters > 0 ? 2 * npx : 0));
     L.total = off;
     return L;
 }
@@ -1027,6 +1107,8 @@ struct Job {
     float *cost_l = nullptr, *cost_r = nullptr, *vol = nullptr;
     int vol_view = 0;
     uchar4 *arms0 = nullptr;   // stage entry point: arms of image 0 go here
+    const int16_t *vsrc = nullptr;   // Eq. 4 round: map voted on (null: no vote)
+    int16_t *vdst = nullptr;         //   and the map written
     Layout L{};
     size_t base = 0;           // workspace offset of this pair
 };
@@ -1149,7 +1231,7 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         if (st != DCO_OK) return st;
     }
     for (auto &kv : vb) {
-        dco_status st = launch_items(h, s, "k_vagg", k_vagg<1>, k_vagg<kBatchMax>, kv.second, kv.first * 32,
+        dco_status st = launch_items(h, s, "k_vagg", k_vagg<1, false>, k_vagg<kBatchMax, false>, kv.second, kv.first * 32,
                                      vsm[kv.first]);
         if (st != DCO_OK) return st;
     }
@@ -1159,6 +1241,84 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
 dco_status launch_lr(dco_stereo *h, const std::vector<Item<LrArgs>> &items, cudaStream_t s)
 {
     return launch_items(h, s, "k_lr", k_lr<1>, k_lr<kBatchMax>, items, 256, 0);
+}
+
+// disparities [d0, d0 + dc) of pass `pass` of one Eq. 4 round, every job
+// with a map to vote on: vote counts per horizontal segment (k_hvote), then
+// vertical sums and the count maximum (k_vagg in vote mode, "k_vvote")
+dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> &jobs, int pass,
+                            cudaStream_t s)
+{
+    std::map<int, std::vector<Item<HVArgs>>> hb;
+    std::map<int, std::vector<Item<VArgs>>> vb;
+    std::map<int, size_t> hsm, vsm;
+    for (const Job &j : jobs) {
+        if (!j.vsrc || pass >= j.L.npass) continue;
+        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
+        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
+        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
+        const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
+        hsm[hg.nw] = std::max(hsm[hg.nw], (size_t)HVSmem(hlen, hg.chunk, hg.nw).total);
+        vsm[vg.nw] = std::max(vsm[vg.nw], vagg_smem_words(vlen, vg.nw) * 4);
+        Item<HVArgs> a{};
+        a.a.disp = j.vsrc;
+        a.a.arms = jptr<uchar4>(h, j, j.L.arms[0]);
+        a.a.sh = jptr<uint32_t>(h, j, j.L.sh[0]);
+        a.a.W = j.W; a.a.H = j.H; a.a.d0 = d0; a.a.dstride = j.L.dstride;
+        a.a.L1 = dv.L1; a.a.chunk = hg.chunk;
+        a.gx = hg.grid.x; a.gy = hg.grid.y; a.gz = (dc + 31) / 32;
+        hb[hg.nw].push_back(a);
+        Item<VArgs> b{};
+        for (int v = 0; v < 2; v++) {
+            b.a.sh[v] = a.a.sh;
+            b.a.arms[v] = a.a.arms;
+            b.a.best[v] = jptr<unsigned long long>(h, j, j.L.best[0]);
+            b.a.disp[v] = j.vdst;
+        }
+        b.a.mask = j.vsrc;
+        b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
+        b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
+        b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        b.gx = vg.grid.x; b.gy = 1; b.gz = vg.grid.z;   // the left view only
+        vb[vg.nw].push_back(b);
+    }
+    for (auto &kv : hb) {
+        dco_status st = launch_items(h, s, "k_hvote", k_hvote<1>, k_hvote<kBatchMax>, kv.second, kv.first * 32,
+                                     hsm[kv.first]);
+        if (st != DCO_OK) return st;
+    }
+    for (auto &kv : vb) {
+        dco_status st = launch_items(h, s, "k_vvote", k_vagg<1, true>, k_vagg<kBatchMax, true>, kv.second,
+                                     kv.first * 32, vsm[kv.first]);
+        if (st != DCO_OK) return st;
+    }
+    return DCO_OK;
+}
+
+// p.vote_iters rounds of Eq. 4 on every job's final map (j.out, in place),
+// alternating with the job's second map; arms of the left view in the
+// workspace
+dco_status run_vote(dco_stereo *h, const dco_params &p, const Derived &dv, std::vector<Job> &jobs, cudaStream_t s)
+{
+    int maxpass = 0;
+    for (const Job &j : jobs) maxpass = std::max(maxpass, j.L.npass);
+    for (int it = 0; it < p.vote_iters; it++) {
+        for (Job &j : jobs) {
+            int16_t *tmp = jptr<int16_t>(h, j, j.L.vtmp);
+            j.vsrc = !j.out ? nullptr : (it & 1) ? tmp : j.out;
+            j.vdst = (it & 1) ? j.out : tmp;
+        }
+        for (int pass = 0; pass < maxpass; pass++) {
+            dco_status st = launch_vote_pass(h, dv, jobs, pass, s);
+            if (st != DCO_OK) return st;
+        }
+    }
+    if (p.vote_iters & 1)
+        for (const Job &j : jobs)
+            if (j.out)
+                DCO_CUDA(h, cudaMemcpyAsync(j.out, jptr<int16_t>(h, j, j.L.vtmp), sizeof(int16_t) * j.W * j.H,
+                                            cudaMemcpyDeviceToDevice, s));
+    return DCO_OK;
 }
 
 // the whole path for a set of independent pairs: one launch per stage
@@ -1189,7 +1349,8 @@ dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, 
         it.gx = (j.W * j.H + 255) / 256; it.gy = 1; it.gz = 1;
         lr.push_back(it);
     }
-    return launch_lr(h, lr, s);
+    if ((st = launch_lr(h, lr, s)) != DCO_OK) return st;
+    return p.vote_iters > 0 ? run_vote(h, p, dv, jobs, s) : DCO_OK;
 }
 
 dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
@@ -1237,6 +1398,7 @@ dco_status dco_params_default(dco_params *p)
     p->tau2 = 6;
     p->lr_tol = 1;
     p->d_chunk = 0;
+    p->vote_iters = 0;
     return DCO_OK;
 }
 
@@ -1409,6 +1571,29 @@ dco_status dco_stereo_arms(dco_stereo *h, const uint8_t *rgb, int W, int H, cons
     if (!rgb || !arms_out || !dims_valid(W, H, 1)) return DCO_EINVAL;
     std::vector<Job> jobs;
     return prep_one(h, p, rgb, W, H, reinterpret_cast<uchar4 *>(arms_out), jobs, (cudaStream_t)stream);
+}
+
+dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *disp_in, int W, int H, int D,
+                           const dco_params *pin, int16_t *disp_out, dco_stream stream)
+{
+    dco_params p;
+    dco_status st = check_common(h, pin, p);
+    if (st != DCO_OK) return st;
+    if (!rgb || !disp_in || !disp_out || !dims_valid(W, H, D)) return DCO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Derived dv;
+    derive(p, dv);
+    std::vector<Job> jobs(1);
+    Job &j = jobs[0];
+    j.left = rgb; j.right = rgb; j.W = W; j.H = H; j.D = D; j.out = disp_out;
+    size_t total = 0;
+    if ((st = plan_jobs(h, p, jobs, total)) != DCO_OK) return st;
+    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+    if ((st = launch_prep(h, p, dv, jobs, 1, s)) != DCO_OK) return st;   // arms of rgb
+    if (disp_in != disp_out)
+        DCO_CUDA(h, cudaMemcpyAsync(disp_out, disp_in, sizeof(int16_t) * W * H, cudaMemcpyDeviceToDevice, s));
+    return run_vote(h, p, dv, jobs, s);
 }
 
 dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H,

@@ -73,6 +73,14 @@ struct HArgs {
     uint32_t Sint;
 };
 
+// horizontal pass of the parallax optimisation (Eq. 4): per-d vote counts
+struct HVArgs {
+    const int16_t *disp;   // map voted on, W x H, -1 = invalid
+    const uchar4 *arms;    // reference-view arms {l, r, u, d}
+    uint32_t *sh;          // count slices [y][x][dstride]
+    int W, H, d0, dstride, L1, chunk;
+};
+
 struct VArgs {
     const uint32_t *sh[2];
     const uchar4 *arms[2];
@@ -80,6 +88,7 @@ struct VArgs {
     int16_t *disp[2];
     float *cost[2];
     float *vol;            // optional (D, H, W) normalised costs of view `vol_view`
+    const int16_t *mask;   // optional: pixels where mask < 0 are written as -1 (vote)
     int vol_view;
     int W, H, D;
     int d0, dc, dstride;
