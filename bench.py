@@ -282,6 +282,7 @@ def own_arm(args):
     # ---- config 3 (batched) and config 4 (serving), rank 0 only
     extras = {}
     if rank == 0 and not args.no_extras:
+        extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
         extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
         extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
@@ -318,6 +319,62 @@ def own_arm(args):
     st.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------- Eq. 4 rounds (config 2)
+def vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 20, rounds: int = 2):
+    """The config 2 path with `rounds` Eq. 4 rounds against the path without,
+    and the vote kernels' own durations (library CUDA events, L2 flushed
+    before every call) against their algorithmic bytes."""
+    W, H = L.shape[1], L.shape[0]
+    npx = W * H
+    out = torch.empty((H, W), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def med_ms(p):
+        for _ in range(3):
+            st.match(L, R, D, p, out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.match(L, R, D, p, out)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    p0 = binding.Params.default(d_chunk=dchunk)
+    pv = binding.Params.default(d_chunk=dchunk, vote_iters=rounds)
+    t0, tv = med_ms(p0), med_ms(pv)
+    st.set_profiling(True)
+    st.profile_reset()
+    for _ in range(reps):
+        flush.zero_()
+        st.match(L, R, D, pv, out)
+    torch.cuda.synchronize(dev)
+    prof = st.profile()
+    st.set_profiling(False)
+    pk, _ = peaks()
+    dc = dchunk or D
+    alg = {"k_hvote": lambda: npx * (2 + 4) + 4 * npx * dc,        # map + arms in, count slice out
+           "k_vvote": lambda: 4 * npx * dc + npx * (4 + 2 + 2)}   # slice + arms + mask in, map out
+    kern = {}
+    round_us = 0.0
+    for k in ("k_hvote", "k_vvote"):
+        if k not in prof:
+            continue
+        n, ms = prof[k]
+        avg_us = ms / n * 1e3
+        round_us += avg_us * n / (reps * rounds)
+        gbs = alg[k]() / (avg_us * 1e-6) / 1e9
+        kern[k] = {"launches_per_round": n / (reps * rounds), "avg_us": round(avg_us, 3),
+                   "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)}
+    return {"rounds": rounds, "ms_path": round(t0, 4), "ms_path_with_rounds": round(tv, 4),
+            "us_per_round": round(round_us, 2),
+            "votes_per_s": npx * D / (round_us * 1e-6) if round_us else None,
+            "kernels": kern}
 
 
 # ------------------------------------------------- config 3 and config 4
