@@ -57,8 +57,8 @@ def parse():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
-            int(os.environ.get("WORLD_SIZE", "1")))
+    from paper_2203_02300_gb300 import replicas
+    return replicas.rank_env()
 
 
 def peaks():
@@ -174,7 +174,7 @@ def own_arm(args):
     import torch
     import torch.distributed as dist
     import __graft_entry__
-    from paper_2203_02300_gb300 import binding, scenes, tune
+    from paper_2203_02300_gb300 import binding, replicas, scenes, tune
 
     rank, local_rank, world = dist_env()
     if world > 1:
@@ -224,12 +224,8 @@ def own_arm(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = W * H * D * args.steps * world
-    value = units / (total_ms * 1e-3)
+    units, total_s, value = replicas.job_rate(W * H * D * args.steps, total_ms * 1e-3, dist, dev)
+    total_ms = total_s * 1e3
 
     # ---- end to end: host buffers through the C ABI (copies inside)
     Ln, Rn = Lh.numpy(), Rh.numpy()
@@ -241,12 +237,7 @@ def own_arm(args):
         t0 = time.perf_counter()
         st.match_host(Ln, Rn, D, p, out=outh)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = units / (e2e_total * 1e-3)
+    _, _, e2e_value = replicas.job_rate(W * H * D * args.steps, sum(e2e_ms) * 1e-3, dist, dev)
     check = st.match(L, R, D, p, out)
     torch.cuda.synchronize(dev)
     assert np.array_equal(outh, check.cpu().numpy()), "host path differs from device path"
