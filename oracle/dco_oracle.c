@@ -367,3 +367,49 @@ int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int 
     free(cur); free(nxt);
     return rc;
 }
+
+/*
+ * Quarter-size input (Sect. 4, Sect. 4.4: the pair is matched at a quarter
+ * of its size).  Reading: half of each axis, every output channel the
+ * rounded mean of its 2x2 input block, (a + b + c + d + 2) >> 2; an odd last
+ * row or column is dropped.  out: (W/2) x (H/2) x 3.
+ */
+int orc_downscale(const uint8_t *rgb, int W, int H, uint8_t *out)
+{
+    if (!rgb || !out || W < 2 || H < 2) return ORC_EINVAL;
+    int Wh = W / 2, Hh = H / 2;
+    for (int y = 0; y < Hh; y++)
+        for (int x = 0; x < Wh; x++)
+            for (int c = 0; c < 3; c++) {
+                int s = rgb[((long)(2 * y) * W + 2 * x) * 3 + c] + rgb[((long)(2 * y) * W + 2 * x + 1) * 3 + c] +
+                        rgb[((long)(2 * y + 1) * W + 2 * x) * 3 + c] +
+                        rgb[((long)(2 * y + 1) * W + 2 * x + 1) * 3 + c];
+                out[((long)y * Wh + x) * 3 + c] = (uint8_t)((s + 2) >> 2);
+            }
+    return ORC_OK;
+}
+
+/*
+ * Sparse depth map (Sect. 4.4, Eq. 14 convention 0 = missing).  The
+ * disparity d of the half-size map is doubled back to full size and
+ * converted with the binocular parameters: Z = f * B / (2 d), f in pixels of
+ * the full image, B the baseline; d <= 0 (invalid or at infinity) gives 0.
+ * Reading of "discretised into the original size": every half-size pixel
+ * covers its 2x2 block of the W x H output; an odd last row or column is 0.
+ */
+int orc_depth(const int16_t *disp_half, int W, int H, double f, double B, double *out)
+{
+    if (!disp_half || !out || W < 2 || H < 2) return ORC_EINVAL;
+    int Wh = W / 2, Hh = H / 2;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int hx = x / 2, hy = y / 2;
+            double z = 0.0;
+            if (hx < Wh && hy < Hh) {
+                int d = disp_half[(long)hy * Wh + hx];
+                if (d > 0) z = f * B / (2.0 * d);
+            }
+            out[(long)y * W + x] = z;
+        }
+    return ORC_OK;
+}

@@ -44,6 +44,10 @@ def lib():
         L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i] + [P] * 9
         L.orc_vote.argtypes = [P, P, i, i, i, i, P]
         L.orc_vote.restype = i
+        L.orc_downscale.argtypes = [P, i, i, P]
+        L.orc_downscale.restype = i
+        L.orc_depth.argtypes = [P, i, i, d, d, P]
+        L.orc_depth.restype = i
         L.orc_grey.restype = i
         L.orc_census.restype = i
         L.orc_hamming.restype = i
@@ -142,6 +146,25 @@ def vote(disp: np.ndarray, arm: np.ndarray, D: int, iters: int = 1) -> np.ndarra
     assert arm.shape == (H, W, 4)
     out = np.empty_like(disp)
     _check(lib().orc_vote(_ptr(disp), _ptr(arm), W, H, D, iters, _ptr(out)))
+    return out
+
+
+def downscale(img: np.ndarray) -> np.ndarray:
+    """Quarter-size input (Sect. 4): 2x2 rounded channel means, (H/2, W/2, 3)."""
+    img = _rgb(img)
+    H, W = img.shape[:2]
+    out = np.empty((H // 2, W // 2, 3), np.uint8)
+    _check(lib().orc_downscale(_ptr(img), W, H, _ptr(out)))
+    return out
+
+
+def depth(disp_half: np.ndarray, W: int, H: int, f: float, B: float) -> np.ndarray:
+    """Sparse depth (Sect. 4.4): Z = f B / (2 d) on the 2x2 block of each
+    half-size pixel of a W x H map; 0 where d <= 0."""
+    disp_half = np.ascontiguousarray(disp_half, np.int16)
+    assert disp_half.shape == (H // 2, W // 2)
+    out = np.empty((H, W), np.float64)
+    _check(lib().orc_depth(_ptr(disp_half), W, H, float(f), float(B), _ptr(out)))
     return out
 
 

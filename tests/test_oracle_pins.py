@@ -513,3 +513,53 @@ def test_vote_iterations_compose():
     once = O.vote(d, a, 12, 1)
     assert np.array_equal(O.vote(d, a, 12, 2), O.vote(once, a, 12, 1))
     assert np.array_equal(O.vote(d, a, 12, 0), d)
+
+
+# ----------------------------------------------------------------- quarter size + depth
+def test_downscale_inverts_block_replication():
+    rng = np.random.default_rng(12)
+    small = rng.integers(0, 256, (13, 17, 3), dtype=np.uint8)
+    big = np.repeat(np.repeat(small, 2, axis=0), 2, axis=1)
+    assert np.array_equal(O.downscale(big), small)
+    # an odd last row and column are dropped
+    odd = np.concatenate([big, rng.integers(0, 256, (1, 34, 3), dtype=np.uint8)], axis=0)
+    odd = np.concatenate([odd, rng.integers(0, 256, (27, 1, 3), dtype=np.uint8)], axis=1)
+    assert np.array_equal(O.downscale(odd), small)
+
+
+def test_downscale_rounds_the_block_mean_half_up():
+    rng = np.random.default_rng(13)
+    img = rng.integers(0, 256, (2, 2 * 500, 3), dtype=np.uint8)
+    out = O.downscale(img)
+    for x in range(500):
+        for c in range(3):
+            vals = [int(img[0, 2 * x, c]), int(img[0, 2 * x + 1, c]), int(img[1, 2 * x, c]), int(img[1, 2 * x + 1, c])]
+            mean = sum(vals) / 4.0
+            assert out[0, x, c] == int(np.floor(mean + 0.5)), (vals, out[0, x, c])
+
+
+def test_depth_closed_forms_and_missing():
+    d = np.array([[2, 0, -1], [4, 1, 7]], np.int16)
+    z = O.depth(d, 7, 5, 700.0, 0.1)
+    assert z.shape == (5, 7)
+    assert z[0, 0] == z[1, 1] == 700.0 * 0.1 / 4          # d = 2 -> 2d = 4 at full size
+    assert z[2, 0] == z[3, 1] == 700.0 * 0.1 / 8
+    assert z[2, 2] == 700.0 * 0.1 / 2 and z[3, 5] == 700.0 * 0.1 / 14
+    assert (z[0:2, 2:6] == 0).all()                       # d = 0 and d = -1: missing
+    assert (z[4, :] == 0).all() and (z[:, 6] == 0).all()  # odd last row / column
+    v = np.repeat(np.repeat(d, 2, axis=0), 2, axis=1)
+    ok = v > 0
+    assert np.allclose(z[:4, :6][ok] * 2 * v[ok], 70.0, rtol=1e-15)   # Z * (2d) = f B
+
+
+def test_quarter_size_path_recovers_a_plane_depth():
+    # a fronto-parallel textured plane at full-size disparity 2*d0: matched at
+    # half size it is found at d0, so its depth is f B / (2 d0)
+    d0, f, B = 6, 800.0, 0.12
+    s = scenes.plane_scene(128, 96, 16, 0, seed=31, drange=(2 * d0, 2 * d0))
+    assert np.allclose(s.disp[:, 2 * d0 + 8:], 2 * d0)
+    Lh, Rh = O.downscale(s.left), O.downscale(s.right)
+    m = O.match(Lh, Rh, 12)
+    z = O.depth(m.disp, 128, 96, f, B)
+    interior = z[8:-8, 2 * (d0 + 8):-8]
+    assert (interior == f * B / (2 * d0)).mean() > 0.95
