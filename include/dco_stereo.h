@@ -196,6 +196,33 @@ dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *dis
                            const dco_params *p, int16_t *disp_out, dco_stream stream);
 
 /*
+ * Quarter-size input alone (Sect. 4): out (device (W/2)*(H/2)*3 bytes) gets
+ * the rounded 2x2 channel means of rgb (device W*H*3 bytes), as used by
+ * dco_stereo_depth.  W, H in [2, 32768].
+ */
+dco_status dco_stereo_downscale(dco_stereo *h, const uint8_t *rgb, int W, int H, uint8_t *out,
+                                dco_stream stream);
+
+/*
+ * Sparse depth at full size (Sect. 4 and 4.4): the pair is reduced to half of
+ * each axis (every channel the rounded mean (a + b + c + d + 2) >> 2 of its
+ * 2x2 block; an odd last row or column is dropped), matched there over D
+ * disparities exactly as dco_stereo_match (both views, consistency check,
+ * p->vote_iters Eq. 4 rounds), and each half-size disparity d is doubled back
+ * and converted with the binocular parameters: Z = f_px * baseline / (2 d)
+ * written to the 2x2 block it covers; 0 marks missing depth (d <= 0, an odd
+ * last row or column), the convention of Eq. 14.
+ * left, right: device W*H*3 bytes (full size).  depth_out: device W*H float,
+ * Z in the unit of `baseline`.  disp_half_out: optional device (W/2)*(H/2)
+ * int16, the half-size map.  f_px > 0 in pixels of the full image,
+ * baseline > 0.  W, H >= 2 and (W/2, H/2, D) must satisfy the limits of
+ * dco_stereo_match; otherwise DCO_EINVAL.
+ */
+dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H, int D,
+                            const dco_params *p, double f_px, double baseline, float *depth_out,
+                            int16_t *disp_half_out, dco_stream stream);
+
+/*
  * Stage a7 alone: left-right consistency.  out(x,y) = dl(x,y) if
  * x - dl >= 0 and |dl - dr(x - dl, y)| <= tol, else -1; tol < 0 copies dl.
  * dl, dr, out: device W*H int16.  The handle is only used for its device.

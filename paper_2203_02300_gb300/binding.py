@@ -85,6 +85,9 @@ def lib():
             "dco_stereo_cost_volume": (c_int, [P, P, P, c_int, c_int, c_int, P, c_int, P, P]),
             "dco_stereo_lr_check": (c_int, [P, P, P, c_int, c_int, c_int, P, P]),
             "dco_stereo_vote": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P]),
+            "dco_stereo_downscale": (c_int, [P, P, c_int, c_int, P, P]),
+            "dco_stereo_depth": (c_int, [P, P, P, c_int, c_int, c_int, P, ctypes.c_double, ctypes.c_double, P, P,
+                                         P]),
             "dco_stereo_match_batch": (c_int, [P, P, c_int, P, P]),
             "dco_stereo_sync_status": (c_int, [P]),
             "dco_stereo_last_error": (ctypes.c_char_p, [P]),
@@ -262,6 +265,27 @@ class Stereo:
         _check(lib().dco_stereo_vote(self._h, _ptr(img), _ptr(disp), W, H, D,
                                      ctypes.byref(params) if params else None, _ptr(out), _stream(stream)),
                self._h)
+        return out
+
+    def downscale(self, img, stream=None):
+        import torch
+        W, H = _rgb_dims(img)
+        out = torch.empty((H // 2, W // 2, 3), dtype=torch.uint8, device=img.device)
+        _check(lib().dco_stereo_downscale(self._h, _ptr(img), W, H, _ptr(out), _stream(stream)), self._h)
+        return out
+
+    def depth(self, left, right, D: int, f_px: float, baseline: float, params: Optional[Params] = None,
+              out=None, disp_half=None, stream=None):
+        """Full-size sparse depth (float32, 0 = missing) from a full-size pair
+        matched at half of each axis over D disparities."""
+        import torch
+        W, H = _rgb_dims(left)
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=left.device)
+        _check(lib().dco_stereo_depth(self._h, _ptr(left), _ptr(right), W, H, D,
+                                      ctypes.byref(params) if params else None, float(f_px), float(baseline),
+                                      _ptr(out), _ptr(disp_half) if disp_half is not None else None,
+                                      _stream(stream)), self._h)
         return out
 
     # -- status and profiling

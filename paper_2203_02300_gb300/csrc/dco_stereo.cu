@@ -654,6 +654,38 @@ __device__ __forceinline__ void lr_body(const LrArgs &a, size_t i)
     a.out[i] = r;
 }
 
+// ------------------------------------------------------ quarter size, depth
+// Sect. 4: the pair is matched at half of each axis; channel c of output
+// pixel (x, y) is the rounded mean (sum + 2) >> 2 of its 2x2 input block.
+__global__ void __launch_bounds__(256) k_down(const DownArgs a)
+{
+    const int Wh = a.W / 2, Hh = a.H / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Wh * Hh) return;
+    const int x = i % Wh, y = i / Wh;
+    const uint8_t *s0 = a.src[blockIdx.y] + ((size_t)(2 * y) * a.W + 2 * x) * 3;
+    const uint8_t *s1 = s0 + (size_t)a.W * 3;
+    uint8_t *d = a.dst[blockIdx.y] + (size_t)i * 3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) d[c] = (uint8_t)((s0[c] + s0[3 + c] + s1[c] + s1[3 + c] + 2) >> 2);
+}
+
+// Sect. 4.4: the half-size disparity doubled back to full size, Z = f B / (2 d)
+// on the 2x2 block of each half-size pixel; 0 (missing, Eq. 14) where d <= 0
+// and on an odd last row or column.
+__global__ void __launch_bounds__(256) k_depth(const DepthArgs a)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.W * a.H) return;
+    const int x = (int)(i % a.W), y = (int)(i / a.W), hx = x >> 1, hy = y >> 1, Wh = a.W / 2;
+    float z = 0.0f;
+    if (hx < Wh && hy < a.H / 2) {
+        const int d = a.disp[(size_t)hy * Wh + hx];
+        if (d > 0) z = a.fb / (2.0f * (float)d);
+    }
+    a.out[i] = z;
+}
+
 // ------------------------------------------------------------------ batches
 // Every stage is one launch over all pairs of a batch (a single pair is a
 // batch of one).  The pairs' arguments travel in the kernel parameters; the
@@ -1321,22 +1353,17 @@ dco_status run_vote(dco_stereo *h, const dco_params &p, const Derived &dv, std::
     return DCO_OK;
 }
 
-// the whole path for a set of independent pairs: one launch per stage
-dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, cudaStream_t s)
+// every stage of the path for planned jobs (workspace and tables ready)
+dco_status launch_jobs(dco_stereo *h, const dco_params &p, const Derived &dv, std::vector<Job> &jobs,
+                       cudaStream_t s)
 {
-    Derived dv;
-    derive(p, dv);
-    size_t total = 0;
-    dco_status st = plan_jobs(h, p, jobs, total);
-    if (st != DCO_OK) return st;
-    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
-    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
     int maxpass = 0;
     for (Job &j : jobs) {
         if (!j.disp_l) j.disp_l = jptr<int16_t>(h, j, j.L.disp[0]);
         if (!j.disp_r) j.disp_r = jptr<int16_t>(h, j, j.L.disp[1]);
         maxpass = std::max(maxpass, j.L.npass);
     }
+    dco_status st;
     if ((st = launch_prep(h, p, dv, jobs, 2, s)) != DCO_OK) return st;
     for (int pass = 0; pass < maxpass; pass++)
         if ((st = launch_pass(h, dv, jobs, pass, s)) != DCO_OK) return st;
@@ -1351,6 +1378,19 @@ dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, 
     }
     if ((st = launch_lr(h, lr, s)) != DCO_OK) return st;
     return p.vote_iters > 0 ? run_vote(h, p, dv, jobs, s) : DCO_OK;
+}
+
+// the whole path for a set of independent pairs: one launch per stage
+dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, cudaStream_t s)
+{
+    Derived dv;
+    derive(p, dv);
+    size_t total = 0;
+    dco_status st = plan_jobs(h, p, jobs, total);
+    if (st != DCO_OK) return st;
+    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+    return launch_jobs(h, p, dv, jobs, s);
 }
 
 dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
@@ -1594,6 +1634,62 @@ dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *dis
     if (disp_in != disp_out)
         DCO_CUDA(h, cudaMemcpyAsync(disp_out, disp_in, sizeof(int16_t) * W * H, cudaMemcpyDeviceToDevice, s));
     return run_vote(h, p, dv, jobs, s);
+}
+
+dco_status dco_stereo_downscale(dco_stereo *h, const uint8_t *rgb, int W, int H, uint8_t *out, dco_stream stream)
+{
+    if (!h || !rgb || !out || W < 2 || H < 2 || W > 2 * 16384 || H > 2 * 16384) return DCO_EINVAL;
+    DCO_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    DownArgs da{};
+    da.src[0] = rgb; da.dst[0] = out; da.W = W; da.H = H;
+    ProfScope ps(h, s, "k_down");
+    k_down<<<dim3((unsigned)(((size_t)(W / 2) * (H / 2) + 255) / 256), 1), 256, 0, s>>>(da);
+    DCO_CUDA(h, cudaGetLastError());
+    return DCO_OK;
+}
+
+dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H, int D,
+                            const dco_params *pin, double f_px, double baseline, float *depth_out,
+                            int16_t *disp_half_out, dco_stream stream)
+{
+    dco_params p;
+    dco_status st = check_common(h, pin, p);
+    if (st != DCO_OK) return st;
+    if (!left || !right || !depth_out || W < 2 || H < 2 || !dims_valid(W / 2, H / 2, D)) return DCO_EINVAL;
+    if (!(f_px > 0.0) || !(baseline > 0.0) || !std::isfinite(f_px * baseline)) return DCO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Wh = W / 2, Hh = H / 2;
+    Derived dv;
+    derive(p, dv);
+    std::vector<Job> jobs(1);
+    Job &j = jobs[0];
+    j.W = Wh; j.H = Hh; j.D = D;
+    size_t total = 0;
+    if ((st = plan_jobs(h, p, jobs, total)) != DCO_OK) return st;
+    // in front of the pair's workspace: the two half-size images and the map
+    const size_t img = align_up(3 * (size_t)Wh * Hh), front = 2 * img + align_up(2 * (size_t)Wh * Hh);
+    j.base = front;
+    if ((st = ensure_ws(h, total + front)) != DCO_OK) return st;
+    if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+    DownArgs da{};
+    da.src[0] = left; da.src[1] = right;
+    da.dst[0] = ws_ptr<uint8_t>(h, 0); da.dst[1] = ws_ptr<uint8_t>(h, img);
+    da.W = W; da.H = H;
+    j.left = da.dst[0]; j.right = da.dst[1];
+    j.out = disp_half_out ? disp_half_out : ws_ptr<int16_t>(h, 2 * img);
+    {
+        ProfScope ps(h, s, "k_down");
+        k_down<<<dim3((unsigned)((Wh * Hh + 255) / 256), 2), 256, 0, s>>>(da);
+        DCO_CUDA(h, cudaGetLastError());
+    }
+    if ((st = launch_jobs(h, p, dv, jobs, s)) != DCO_OK) return st;
+    DepthArgs za{};
+    za.disp = j.out; za.out = depth_out; za.W = W; za.H = H; za.fb = (float)(f_px * baseline);
+    ProfScope ps(h, s, "k_depth");
+    k_depth<<<(unsigned)(((size_t)W * H + 255) / 256), 256, 0, s>>>(za);
+    DCO_CUDA(h, cudaGetLastError());
+    return DCO_OK;
 }
 
 dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H,

@@ -81,6 +81,21 @@ struct HVArgs {
     int W, H, d0, dstride, L1, chunk;
 };
 
+// quarter-size input (Sect. 4): the two images of a pair, W x H -> W/2 x H/2
+struct DownArgs {
+    const uint8_t *src[2];
+    uint8_t *dst[2];
+    int W, H;
+};
+
+// sparse depth (Sect. 4.4) of a half-size map on the W x H grid
+struct DepthArgs {
+    const int16_t *disp;   // (H/2) x (W/2)
+    float *out;            // W x H
+    int W, H;
+    float fb;              // f * B
+};
+
 struct VArgs {
     const uint32_t *sh[2];
     const uchar4 *arms[2];
