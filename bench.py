@@ -274,6 +274,7 @@ def own_arm(args):
     extras = {}
     if rank == 0 and not args.no_extras:
         extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
         extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
         extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
         extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
@@ -366,6 +367,55 @@ def vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 20
             "us_per_round": round(round_us, 2),
             "votes_per_s": npx * D / (round_us * 1e-6) if round_us else None,
             "kernels": kern}
+
+
+# ------------------------------------------- quarter size + depth (Sect. 4.4)
+def depth_full_size(torch, binding, st, flush, dev, W: int = 1280, H: int = 720, D: int = 64, reps: int = 20):
+    """A 1280x720 pair (the sensor size the paper reduces by a quarter):
+    downscale to 640x360, match over D = 64 half-size disparities, depth on
+    the full grid.  Median CUDA-event time per frame (L2 flushed before each)
+    and the two new kernels against their algorithmic bytes."""
+    from paper_2203_02300_gb300 import scenes
+    s = scenes.plane_scene(W, H, 2 * D, 12, seed=scenes.seed_for(2, 900), drange=(4, 2 * D - 8),
+                           slanted=True, slope=0.2, noise_sigma=2.0)
+    L = torch.from_numpy(s.left).to(dev)
+    R = torch.from_numpy(s.right).to(dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        st.depth(L, R, D, 700.0, 0.12, out=out)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.depth(L, R, D, 700.0, 0.12, out=out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    st.set_profiling(True)
+    st.profile_reset()
+    for _ in range(reps):
+        flush.zero_()
+        st.depth(L, R, D, 700.0, 0.12, out=out)
+    torch.cuda.synchronize(dev)
+    prof = st.profile()
+    st.set_profiling(False)
+    pk, _ = peaks()
+    npx, nh = W * H, (W // 2) * (H // 2)
+    alg = {"k_down": 2 * (3 * npx + 3 * nh), "k_depth": 2 * nh + 4 * npx}
+    kern = {}
+    for k, (n, ms) in prof.items():
+        avg = ms / n * 1e3
+        e = {"avg_us": round(avg, 3)}
+        if k in alg:
+            gbs = alg[k] / (avg * 1e-6) / 1e9
+            e.update(achieved_gbs=round(gbs, 1), frac_hbm=round(gbs / pk["hbm_gbs"], 4))
+        kern[k] = e
+    med = statistics.median(ts)
+    return {"input": f"{W}x{H}", "matched_at": f"{W // 2}x{H // 2} D={D}", "ms_per_frame": round(med, 4),
+            "frames_per_s": 1e3 / med, "evals_per_s": nh * D / (med * 1e-3),
+            "valid_fraction": float((out > 0).float().mean().item()), "kernels": kern}
 
 
 # ------------------------------------------------- config 3 and config 4

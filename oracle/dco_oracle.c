@@ -25,6 +25,10 @@
  *     p + j e lies in the image, Dc(p_j, p) < tau1, Dc(p_j, p_{j-1}) < tau1,
  *     and Dc(p_j, p) < tau2 whenever j > L2; Dc = max channel difference.
  *   - L_min = the shortest of the four arms of p (Eq. 1).
+ *   - smooth cross-support window (Sect. 4.1, "morphological processing";
+ *     the figure is missing), when enabled: a grey-level opening of each of
+ *     the four arm-length maps (3x3 minimum, then 3x3 maximum, windows cut to
+ *     the image); L_min and the regions use the opened arms.
  *   - support region (Eq. 2): union over q on the vertical arm of p of q's
  *     horizontal segment; N = its pixel count.  Reference-view arms only.
  *   - d in [0, D-1]; a match outside the image costs 1 (upper bound of Eq. 1).
@@ -147,6 +151,38 @@ typedef struct {
 } orc_cost_params;
 
 /* Eq. 1: adaptive weight from the shortest arm */
+/*
+ * Morphological smoothing of the cross-support window (Sect. 4.1): opening
+ * of every arm-length map, out(p) = max over q in W(p) of min over r in W(q)
+ * of arms(r), W(p) the 3x3 window around p cut to the image.  An opening
+ * never lengthens an arm, so the result stays inside the image and <= L1.
+ */
+int orc_arms_smooth(const uint8_t *arms, int W, int H, uint8_t *out)
+{
+    if (!arms || !out || W < 1 || H < 1) return ORC_EINVAL;
+    long n = (long)W * H;
+    uint8_t *er = (uint8_t *)malloc(4 * n);
+    if (!er) return ORC_ENOMEM;
+    for (int pass = 0; pass < 2; pass++) {
+        const uint8_t *src = pass == 0 ? arms : er;
+        uint8_t *dst = pass == 0 ? er : out;
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++)
+                for (int k = 0; k < 4; k++) {
+                    int v = pass == 0 ? 255 : 0;
+                    for (int yy = y - 1; yy <= y + 1; yy++)
+                        for (int xx = x - 1; xx <= x + 1; xx++) {
+                            if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                            int a = src[4 * ((long)yy * W + xx) + k];
+                            v = pass == 0 ? (a < v ? a : v) : (a > v ? a : v);
+                        }
+                    dst[4 * ((long)y * W + x) + k] = (uint8_t)v;
+                }
+    }
+    free(er);
+    return ORC_OK;
+}
+
 double orc_alpha(int lmin, double gamma_l, double eps)
 {
     return 1.0 - exp(-gamma_l / ((double)lmin + eps));
@@ -288,7 +324,7 @@ int orc_lr_check(const int16_t *dl, const int16_t *dr, int W, int rows, int tol,
  */
 int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
               double lambda_ad, double lambda_census, double gamma_l, double eps,
-              int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol,
+              int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol, int smooth,
               int y0, int y1,
               int16_t *disp_l, int16_t *disp_r, int16_t *disp_final,
               double *best_l, double *second_l, double *best_r, double *second_r,
@@ -306,6 +342,10 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
     if ((rc = orc_census(right, W, H, cw, ch, cr)) != ORC_OK) goto done;
     if ((rc = orc_arms(left, W, H, L1, L2, tau1, tau2, al)) != ORC_OK) goto done;
     if ((rc = orc_arms(right, W, H, L1, L2, tau1, tau2, ar)) != ORC_OK) goto done;
+    if (smooth) {
+        if ((rc = orc_arms_smooth(al, W, H, al)) != ORC_OK) goto done;
+        if ((rc = orc_arms_smooth(ar, W, H, ar)) != ORC_OK) goto done;
+    }
     {
         orc_cost_params cp = {lambda_ad, lambda_census, gamma_l, eps};
         view_ctx vl = {W, H, D, left, right, cl, cr, al, -1, cp};

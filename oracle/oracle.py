@@ -41,7 +41,9 @@ def lib():
         L.orc_cost_terms.argtypes = [i, i, i, d, d, d, d]
         L.orc_cost_terms.restype = d
         L.orc_lr_check.argtypes = [P, P, i, i, i, P]
-        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i] + [P] * 9
+        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i] + [P] * 9
+        L.orc_arms_smooth.argtypes = [P, i, i, P]
+        L.orc_arms_smooth.restype = i
         L.orc_vote.argtypes = [P, P, i, i, i, i, P]
         L.orc_vote.restype = i
         L.orc_downscale.argtypes = [P, i, i, P]
@@ -72,6 +74,7 @@ class Params:
     tau1: int = 20
     tau2: int = 6
     lr_tol: int = 1               # reading; < 0 disables the check
+    smooth_arms: int = 0          # reading of Sect. 4.1's morphological processing; 1 = 3x3 opening
 
 
 def _ptr(a: np.ndarray):
@@ -115,6 +118,17 @@ def arms(img: np.ndarray, p: Params = Params()) -> np.ndarray:
     H, W, _ = img.shape
     out = np.empty((H, W, 4), np.uint8)
     _check(lib().orc_arms(_ptr(img), W, H, p.arm_l1, p.arm_l2, p.tau1, p.tau2, _ptr(out)))
+    if p.smooth_arms:
+        _check(lib().orc_arms_smooth(_ptr(out), W, H, _ptr(out)))
+    return out
+
+
+def arms_smooth(arm: np.ndarray) -> np.ndarray:
+    """Sect. 4.1 smoothing: grey-level 3x3 opening of each arm-length map."""
+    arm = np.ascontiguousarray(arm, np.uint8)
+    H, W, _ = arm.shape
+    out = np.empty_like(arm)
+    _check(lib().orc_arms_smooth(_ptr(arm), W, H, _ptr(out)))
     return out
 
 
@@ -200,7 +214,7 @@ def match(left: np.ndarray, right: np.ndarray, D: int, p: Params = Params(),
     null = ctypes.c_void_p(0)
     _check(lib().orc_match(_ptr(left), _ptr(right), W, H, D, p.lambda_ad, p.lambda_census,
                            p.gamma_l, p.eps, p.census_w, p.census_h, p.arm_l1, p.arm_l2,
-                           p.tau1, p.tau2, p.lr_tol, y0, y1,
+                           p.tau1, p.tau2, p.lr_tol, p.smooth_arms, y0, y1,
                            _ptr(dl), _ptr(dr), _ptr(df), _ptr(bl), _ptr(sl), _ptr(br), _ptr(sr),
                            _ptr(vl) if volume else null, _ptr(vr) if volume else null))
     return MatchResult(dl, dr, df, bl, sl, br, sr, vl, vr, y0)

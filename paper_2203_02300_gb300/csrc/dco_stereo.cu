@@ -660,30 +660,35 @@ __device__ __forceinline__ void lr_body(const LrArgs &a, size_t i)
 __global__ void __launch_bounds__(256) k_down(const DownArgs a)
 {
     const int Wh = a.W / 2, Hh = a.H / 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Wh * Hh) return;
-    const int x = i % Wh, y = i / Wh;
-    const uint8_t *s0 = a.src[blockIdx.y] + ((size_t)(2 * y) * a.W + 2 * x) * 3;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= Wh || y >= Hh) return;
+    const uint8_t *s0 = a.src[blockIdx.z] + ((size_t)(2 * y) * a.W + 2 * x) * 3;
     const uint8_t *s1 = s0 + (size_t)a.W * 3;
-    uint8_t *d = a.dst[blockIdx.y] + (size_t)i * 3;
+    uint8_t *d = a.dst[blockIdx.z] + ((size_t)y * Wh + x) * 3;
 #pragma unroll
     for (int c = 0; c < 3; c++) d[c] = (uint8_t)((s0[c] + s0[3 + c] + s1[c] + s1[3 + c] + 2) >> 2);
 }
 
 // Sect. 4.4: the half-size disparity doubled back to full size, Z = f B / (2 d)
 // on the 2x2 block of each half-size pixel; 0 (missing, Eq. 14) where d <= 0
-// and on an odd last row or column.
+// and on an odd last row or column.  Thread = one 2x2 block (hx, hy) of the
+// ceil(W/2) x ceil(H/2) blocks.
 __global__ void __launch_bounds__(256) k_depth(const DepthArgs a)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)a.W * a.H) return;
-    const int x = (int)(i % a.W), y = (int)(i / a.W), hx = x >> 1, hy = y >> 1, Wh = a.W / 2;
+    const int hx = blockIdx.x * blockDim.x + threadIdx.x, hy = blockIdx.y;
+    if (2 * hx >= a.W) return;
+    const int Wh = a.W / 2;
     float z = 0.0f;
     if (hx < Wh && hy < a.H / 2) {
         const int d = a.disp[(size_t)hy * Wh + hx];
         if (d > 0) z = a.fb / (2.0f * (float)d);
     }
-    a.out[i] = z;
+    const int x = 2 * hx;
+    for (int y = 2 * hy; y < min(a.H, 2 * hy + 2); y++) {
+        float *o = a.out + (size_t)y * a.W + x;
+        o[0] = z;
+        if (x + 1 < a.W) o[1] = z;
+    }
 }
 
 // ------------------------------------------------------------------ batches
@@ -1644,7 +1649,7 @@ dco_status dco_stereo_downscale(dco_stereo *h, const uint8_t *rgb, int W, int H,
     DownArgs da{};
     da.src[0] = rgb; da.dst[0] = out; da.W = W; da.H = H;
     ProfScope ps(h, s, "k_down");
-    k_down<<<dim3((unsigned)(((size_t)(W / 2) * (H / 2) + 255) / 256), 1), 256, 0, s>>>(da);
+    k_down<<<dim3((unsigned)((W / 2 + 255) / 256), (unsigned)(H / 2), 1), 256, 0, s>>>(da);
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
 }
@@ -1680,14 +1685,14 @@ dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *r
     j.out = disp_half_out ? disp_half_out : ws_ptr<int16_t>(h, 2 * img);
     {
         ProfScope ps(h, s, "k_down");
-        k_down<<<dim3((unsigned)((Wh * Hh + 255) / 256), 2), 256, 0, s>>>(da);
+        k_down<<<dim3((unsigned)((Wh + 255) / 256), (unsigned)Hh, 2), 256, 0, s>>>(da);
         DCO_CUDA(h, cudaGetLastError());
     }
     if ((st = launch_jobs(h, p, dv, jobs, s)) != DCO_OK) return st;
     DepthArgs za{};
     za.disp = j.out; za.out = depth_out; za.W = W; za.H = H; za.fb = (float)(f_px * baseline);
     ProfScope ps(h, s, "k_depth");
-    k_depth<<<(unsigned)(((size_t)W * H + 255) / 256), 256, 0, s>>>(za);
+    k_depth<<<dim3((unsigned)(((W + 1) / 2 + 255) / 256), (unsigned)((H + 1) / 2)), 256, 0, s>>>(za);
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
 }

@@ -563,3 +563,54 @@ def test_quarter_size_path_recovers_a_plane_depth():
     z = O.depth(m.disp, 128, 96, f, B)
     interior = z[8:-8, 2 * (d0 + 8):-8]
     assert (interior == f * B / (2 * d0)).mean() > 0.95
+
+
+# ----------------------------------------------------------------- arm smoothing (Sect. 4.1)
+def test_arm_smoothing_is_the_library_grey_opening():
+    from scipy import ndimage
+    rng = np.random.default_rng(21)
+    for H, W in ((1, 1), (2, 7), (17, 23)):
+        a = rng.integers(0, 35, (H, W, 4)).astype(np.uint8)
+        want = np.stack([ndimage.grey_opening(a[..., k], size=(3, 3), mode="nearest") for k in range(4)], axis=-1)
+        assert np.array_equal(O.arms_smooth(a), want), (H, W)
+
+
+def test_arm_smoothing_is_an_opening():
+    s = scenes.plane_scene(60, 40, 16, 4, seed=22, drange=(1, 14), noise_sigma=3.0)
+    a = O.arms(s.left)
+    o = O.arms_smooth(a)
+    assert (o <= a).all()                                  # anti-extensive
+    assert np.array_equal(O.arms_smooth(o), o)             # idempotent
+    assert np.array_equal(O.arms(s.left, O.Params(smooth_arms=1)), o)
+    ys, xs = np.mgrid[0:40, 0:60]
+    room = np.stack([xs, 59 - xs, ys, 39 - ys], axis=-1)
+    assert (o <= room).all()                               # still inside the image
+
+
+def test_arm_smoothing_removes_spikes_keeps_plateaus():
+    a = np.full((9, 9, 4), 2, np.uint8)
+    a[1, 1, 0] = 30                 # isolated long arm: gone
+    a[4:7, 4:7, 1] = 20             # 3x3 plateau: kept
+    o = O.arms_smooth(a)
+    assert o[1, 1, 0] == 2
+    assert (o[4:7, 4:7, 1] == 20).all() and (o[..., 1].sum() - 9 * 20) == (81 - 9) * 2
+
+
+def test_match_with_smoothing_aggregates_over_the_opened_arms():
+    # the region mean of Eq. 2 by explicit coordinate sets, with L_min and the
+    # regions taken from the opened arms (the opening itself is pinned above)
+    rng = np.random.default_rng(24)
+    base = rng.integers(0, 256, (3, 4, 3))
+    left = np.clip(np.kron(base, np.ones((4, 4, 1))) + rng.integers(-8, 9, (12, 16, 3)), 0, 255).astype(np.uint8)
+    right = np.roll(left, -2, axis=1)
+    p = O.Params(arm_l1=5, arm_l2=2, smooth_arms=1)
+    res = O.match(left, right, 5, p, volume=True)
+    C, al = _raw_costs_left(left, right, 5, p)
+    assert np.array_equal(al, O.arms_smooth(O.arms(left, O.Params(arm_l1=5, arm_l2=2))))
+    assert not np.array_equal(al, O.arms(left, O.Params(arm_l1=5, arm_l2=2)))
+    for y in range(12):
+        for x in range(16):
+            pts = _region(al, x, y)
+            for d in range(5):
+                ref = sum(C[d, yy, xx] for xx, yy in pts) / len(pts)
+                assert res.vol_l[d, y, x] == pytest.approx(ref, rel=1e-12, abs=1e-15)
