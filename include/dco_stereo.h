@@ -70,7 +70,11 @@ typedef enum {
  *   when j > arm_l2, < tau2 to p (defaults 34, 17, 20, 6);
  *   lr_tol = 1 (a negative value disables the consistency check);
  *   vote_iters = 0: rounds of the parallax optimisation of Sect. 4.3 (Eq. 4)
- *   applied to the checked map (see dco_stereo_vote), 0..64.
+ *   applied to the checked map (see dco_stereo_vote), 0..64;
+ *   smooth_arms = 0: with 1, the "morphological processing" of Sect. 4.1 is
+ *   read as a grey-level opening (3x3 minimum, then 3x3 maximum, windows cut
+ *   to the image) of each arm map; L_min, alpha and the support regions then
+ *   follow the opened arms (dco_stereo_arms returns them too).
  */
 typedef struct {
     float lambda_ad;
@@ -86,6 +90,7 @@ typedef struct {
     int lr_tol;
     int d_chunk; /* disparities aggregated per pass (0 = automatic); see dco_stereo_match */
     int vote_iters; /* Eq. 4 rounds after the consistency check (0 = none) */
+    int smooth_arms; /* 1: smooth cross-support window (Sect. 4.1), see above; 0 = raw arms */
 } dco_params;
 
 /* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */

@@ -238,6 +238,36 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     (img ? a.arms[1] : a.arms[0])[i] = make_uchar4((uint8_t)arm[0], (uint8_t)arm[1], (uint8_t)arm[2], (uint8_t)arm[3]);
 }
 
+// --------------------------------------------------------------- k_smooth
+// Smooth cross-support window (Sect. 4.1, morphological processing): the
+// opening of each arm map is a 3x3 minimum (kMax = false) followed by a 3x3
+// maximum (kMax = true), windows cut to the image.  An opening never
+// lengthens an arm, so arms stay inside the image and <= L1.  The maximum
+// pass also rewrites the record's L_min and alpha(L_min)*S (Eq. 1).
+template <bool kMax>
+__device__ __forceinline__ void smooth_body(const SmoothArgs &a, int i, int img)
+{
+    if (i >= a.W * a.H) return;
+    const int x = i % a.W, y = i / a.W;
+    const uchar4 *src = img ? a.src[1] : a.src[0];
+    int v[4] = {kMax ? 0 : 255, kMax ? 0 : 255, kMax ? 0 : 255, kMax ? 0 : 255};
+    for (int yy = max(0, y - 1); yy <= min(a.H - 1, y + 1); yy++)
+        for (int xx = max(0, x - 1); xx <= min(a.W - 1, x + 1); xx++) {
+            const uchar4 q = src[(size_t)yy * a.W + xx];
+            const int c[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = kMax ? max(v[k], c[k]) : min(v[k], c[k]);
+        }
+    (img ? a.dst[1] : a.dst[0])[i] = make_uchar4((uint8_t)v[0], (uint8_t)v[1], (uint8_t)v[2], (uint8_t)v[3]);
+    uint4 *rec = img ? a.rec[1] : a.rec[0];
+    if (kMax && rec) {
+        const int lmin = min(min(v[0], v[1]), min(v[2], v[3]));
+        uint4 *r = rec + (size_t)y * a.rpitch + x;
+        r->z = (r->z & 0x00ffffffu) | (uint32_t(lmin) << 24);
+        r->w = __float_as_uint(__ldg(a.tables + kTabAD + kTabCen + lmin));
+    }
+}
+
 // ------------------------------------------------------------------ k_hagg
 // Block = one row segment of one reference view for one group of 32
 // disparities (lane = disparity d0 + 32*g + lane).  Stage 0 copies (cp.async)
@@ -720,6 +750,14 @@ __device__ __forceinline__ int batch_pair(const Batch<A, N> &b, int flat, int &b
     return lo;
 }
 
+template <int N, bool kMax>
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ Batch<SmoothArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    smooth_body<kMax>(b.p[i], bx * 256 + threadIdx.x, by);
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Batch<PackArgs, N> b)
 {
@@ -802,7 +840,7 @@ struct Derived {
 };
 
 struct Layout {
-    size_t rgbx[2], grey[2], rec[2], arms[2], best[2], disp[2], sh[2], vtmp, total;
+    size_t rgbx[2], grey[2], rec[2], arms[2], atmp[2], best[2], disp[2], sh[2], vtmp, total;
     int dc, dstride, npass, rpitch;
 };
 
@@ -831,6 +869,7 @@ bool params_valid(const dco_params &p)
     if (p.arm_l1 < 1 || p.arm_l1 > kMaxL1 || p.arm_l2 < 0 || p.tau1 < 0 || p.tau2 < 0) return false;
     if (p.d_chunk < 0) return false;
     if (p.vote_iters < 0 || p.vote_iters > 64) return false;
+    if (p.smooth_arms != 0 && p.smooth_arms != 1) return false;
     return true;
 }
 
@@ -865,6 +904,7 @@ Layout make_layout(int W, int H, int D, const dco_params &p, int dc_override = 0
     for (int v = 0; v < 2; v++) { L.grey[v] = off; off = align_up(off + npx); }
     for (int v = 0; v < 2; v++) { L.rec[v] = off; off = align_up(off + 16 * (size_t)H * L.rpitch); }
     for (int v = 0; v < 2; v++) { L.arms[v] = off; off = align_up(off + 4 * npx); }
+    for (int v = 0; v < 2; v++) { L.atmp[v] = off; off = align_up(off + (p.smooth_arms ? 4 * npx : 0)); }
     for (int v = 0; v < 2; v++) { L.best[v] = off; off = align_up(off + (L.npass > 1 ? 8 * npx : 0)); }
     for (int v = 0; v < 2; v++) { L.disp[v] = off; off = align_up(off + 2 * npx); }
     for (int v = 0; v < 2; v++) { L.sh[v] = off; off = align_up(off + 4 * npx * (size_t)L.dstride); }
@@ -1214,8 +1254,34 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
     dco_status st = launch_items(h, s, "k_pack", k_pack<1>, k_pack<kBatchMax>, pk, 256, 0);
     if (st != DCO_OK) return st;
     if (p.census_w == 9 && p.census_h == 7)
-        return launch_items(h, s, "k_prep", k_prep<9, 7, 1>, k_prep<9, 7, kBatchMax>, pr, kTX * kTY, 0);
-    return launch_items(h, s, "k_prep", k_prep<0, 0, 1>, k_prep<0, 0, kBatchMax>, pr, kTX * kTY, 0);
+        st = launch_items(h, s, "k_prep", k_prep<9, 7, 1>, k_prep<9, 7, kBatchMax>, pr, kTX * kTY, 0);
+    else
+        st = launch_items(h, s, "k_prep", k_prep<0, 0, 1>, k_prep<0, 0, kBatchMax>, pr, kTX * kTY, 0);
+    if (st != DCO_OK || !p.smooth_arms) return st;
+    // Sect. 4.1 smoothing: arms -> 3x3 minimum (atmp) -> 3x3 maximum (arms, records)
+    std::vector<Item<SmoothArgs>> er, di;
+    for (size_t k = 0; k < jobs.size(); k++) {
+        const Job &j = jobs[k];
+        Item<SmoothArgs> e{};
+        for (int v = 0; v < 2; v++) {
+            e.a.src[v] = pr[k].a.arms[v];
+            e.a.dst[v] = jptr<uchar4>(h, j, j.L.atmp[v]);
+        }
+        e.a.tables = h->d_tables;
+        e.a.W = j.W; e.a.H = j.H; e.a.rpitch = j.L.rpitch;
+        e.gx = (j.W * j.H + 255) / 256; e.gy = nimg; e.gz = 1;
+        er.push_back(e);
+        Item<SmoothArgs> d = e;
+        for (int v = 0; v < 2; v++) {
+            d.a.src[v] = e.a.dst[v];
+            d.a.dst[v] = pr[k].a.arms[v];
+            d.a.rec[v] = pr[k].a.rec[v];
+        }
+        di.push_back(d);
+    }
+    if ((st = launch_items(h, s, "k_smooth", k_smooth<1, false>, k_smooth<kBatchMax, false>, er, 256, 0)) != DCO_OK)
+        return st;
+    return launch_items(h, s, "k_smooth", k_smooth<1, true>, k_smooth<kBatchMax, true>, di, 256, 0);
 }
 
 // pass `pass` (disparities [pass*dc, pass*dc + dc)) of every job that has it.
@@ -1444,6 +1510,7 @@ dco_status dco_params_default(dco_params *p)
     p->lr_tol = 1;
     p->d_chunk = 0;
     p->vote_iters = 0;
+    p->smooth_arms = 0;
     return DCO_OK;
 }
 

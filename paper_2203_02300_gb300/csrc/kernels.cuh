@@ -96,6 +96,16 @@ struct DepthArgs {
     float fb;              // f * B
 };
 
+// smoothing of the cross-support window (Sect. 4.1): one pass of a 3x3
+// grey-level opening (minimum, then maximum) of the four arm maps
+struct SmoothArgs {
+    const uchar4 *src[2];
+    uchar4 *dst[2];
+    uint4 *rec[2];         // dilation pass: records whose L_min and alpha*S follow the new arms
+    const float *tables;
+    int W, H, rpitch;
+};
+
 struct VArgs {
     const uint32_t *sh[2];
     const uchar4 *arms[2];

@@ -146,3 +146,15 @@ def test_handles_never_lower_each_others_kernel_limits(env):
     assert np.array_equal(r1, r2)
     a.close()
     b.close()
+
+
+def test_batch_with_smoothing_equals_single(env, config3):
+    torch, binding, st = env
+    p = binding.Params.default(smooth_arms=1)
+    sub = config3[:6]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")) for s in sub]
+    st.match_batch(pairs, p)
+    torch.cuda.synchronize()
+    for s, (_, _, _, out) in zip(sub, pairs):
+        assert np.array_equal(out.cpu().numpy(), _single(env, s, p))

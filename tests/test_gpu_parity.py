@@ -35,7 +35,7 @@ def oparams(bp):
     return O.Params(lambda_ad=float(bp.lambda_ad), lambda_census=float(bp.lambda_census),
                     gamma_l=float(bp.gamma_l), eps=float(bp.eps), census_w=bp.census_w,
                     census_h=bp.census_h, arm_l1=bp.arm_l1, arm_l2=bp.arm_l2, tau1=bp.tau1,
-                    tau2=bp.tau2, lr_tol=bp.lr_tol)
+                    tau2=bp.tau2, lr_tol=bp.lr_tol, smooth_arms=bp.smooth_arms)
 
 
 def run_views(env, left, right, D, bp=None):
@@ -83,6 +83,16 @@ def test_arms_bit_exact(env, k):
     img = stage_images()[k]
     got = st.arms(dev(torch, img)).cpu().numpy()
     assert (got == O.arms(img)).all()
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_smoothed_arms_bit_exact(env, k):
+    # Sect. 4.1 smoothing (3x3 opening): integer work, bit-exact
+    torch, binding, st = env
+    img = stage_images()[k]
+    bp = binding.Params.default(smooth_arms=1)
+    got = st.arms(dev(torch, img), bp).cpu().numpy()
+    assert np.array_equal(got, O.arms(img, oparams(bp)))
 
 
 def test_census_and_arms_other_windows(env):
@@ -162,7 +172,8 @@ def test_identical_views(env):
 
 @pytest.mark.parametrize("over", [dict(lr_tol=-1), dict(lr_tol=0), dict(arm_l1=5, arm_l2=2),
                                   dict(gamma_l=3.0, eps=0.5), dict(lambda_ad=30.0, lambda_census=15.0),
-                                  dict(census_w=7, census_h=5), dict(arm_l1=40, arm_l2=40, tau1=256, tau2=256)])
+                                  dict(census_w=7, census_h=5), dict(arm_l1=40, arm_l2=40, tau1=256, tau2=256),
+                                  dict(smooth_arms=1), dict(smooth_arms=1, arm_l1=5, arm_l2=2)])
 def test_parameter_variants(env, over):
     torch, binding, st = env
     s = scenes.config_scene(1)

@@ -115,3 +115,13 @@ def test_vote_rejects_bad_rounds(env):
     with pytest.raises(binding.DcoError) as e:
         st.vote(img, d, 4, binding.Params.default(vote_iters=65))
     assert e.value.code == binding.DCO_EINVAL
+
+
+def test_vote_over_smoothed_arms(env):
+    torch, binding, st = env
+    rng = np.random.default_rng(10)
+    s = scenes.plane_scene(120, 90, 24, 5, seed=scenes.seed_for(1, 330), drange=(1, 22), noise_sigma=2.0)
+    d = _noisy_map(rng, s, 24)
+    p = binding.Params.default(vote_iters=2, smooth_arms=1)
+    got = st.vote(_dev(torch, s.left), _dev(torch, d), 24, p).cpu().numpy()
+    assert np.array_equal(got, O.vote(d, O.arms(s.left, O.Params(smooth_arms=1)), 24, 2))
