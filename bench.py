@@ -275,6 +275,7 @@ def own_arm(args):
     if rank == 0 and not args.no_extras:
         extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
+        extras["smooth_config2"] = smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
         extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
         extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
@@ -367,6 +368,46 @@ def vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 20
             "us_per_round": round(round_us, 2),
             "votes_per_s": npx * D / (round_us * 1e-6) if round_us else None,
             "kernels": kern}
+
+
+# ------------------------------------ arm smoothing, Sect. 4.1 (config 2)
+def smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 20):
+    """The config 2 path with the smoothed cross-support window against the
+    path without; the smoothing kernel's duration against its bytes."""
+    W, H = L.shape[1], L.shape[0]
+    out = torch.empty((H, W), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def med_ms(p):
+        for _ in range(3):
+            st.match(L, R, D, p, out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.match(L, R, D, p, out)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    p1 = binding.Params.default(d_chunk=dchunk, smooth_arms=1)
+    t0, t1 = med_ms(binding.Params.default(d_chunk=dchunk)), med_ms(p1)
+    st.set_profiling(True)
+    st.profile_reset()
+    for _ in range(reps):
+        flush.zero_()
+        st.match(L, R, D, p1, out)
+    torch.cuda.synchronize(dev)
+    n, ms = st.profile().get("k_smooth", (0, 0.0))
+    st.set_profiling(False)
+    pk, _ = peaks()
+    avg = ms / n * 1e3 if n else None
+    alg = 2 * W * H * (4 + 4) + W * H * 8   # per pass: arms in/out (both images); records touched once
+    return {"ms_path": round(t0, 4), "ms_path_smoothed": round(t1, 4),
+            "k_smooth": {"launches_per_frame": n / reps, "avg_us": round(avg, 3) if avg else None,
+                         "frac_hbm": round(alg / (avg * 1e-6) / 1e9 / pk["hbm_gbs"], 4) if avg else None}}
 
 
 # ------------------------------------------- quarter size + depth (Sect. 4.4)

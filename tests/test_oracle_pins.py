@@ -614,3 +614,68 @@ def test_match_with_smoothing_aggregates_over_the_opened_arms():
             for d in range(5):
                 ref = sum(C[d, yy, xx] for xx, yy in pts) / len(pts)
                 assert res.vol_l[d, y, x] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+
+
+# ----------------------------------------------------------------- densification (Sect. 6)
+from oracle import densify as DN   # noqa: E402
+
+
+def _dn_inputs(rng, H, W, frac=0.1, contour=False):
+    ds = np.where(rng.random((H, W)) < frac, rng.uniform(0.5, 5.0, (H, W)), 0.0)
+    B = (rng.random((H, W)) < 0.15).astype(np.uint8) if contour else np.zeros((H, W), np.uint8)
+    return ds, B, rng.random((H, W)), rng.random((H, W))
+
+
+def test_densify_pair_weight_cases():
+    assert DN.pair_weight(1, 0, 0.1, 0.2) == 0.0 and DN.pair_weight(0, 1, 0.0, 0.0) == 0.0   # Eq. 16 first case
+    assert DN.pair_weight(1, 1, 0.3, 0.6) == pytest.approx(0.7)
+    assert DN.pair_weight(0, 0, 0.3, 0.6) == pytest.approx(0.7)
+    assert DN.pair_weight(0, 0, 1.5, 2.0) == 0.0                                            # max(., 0)
+
+
+def test_densify_without_smoothness_is_the_weighted_data_mean():
+    rng = np.random.default_rng(41)
+    ds, B, mf, mi = _dn_inputs(rng, 6, 7, 0.5)
+    dp = np.where(rng.random((6, 7)) < 0.5, rng.uniform(1, 3, (6, 7)), 0.0)
+    p = DN.DenseParams(lambda_d=0.8, lambda_s=0.0, lambda_s2=0.3)
+    D = DN.densify(ds, B, mf, mi, dp, p)
+    ws, wt = (ds > 0) * 0.8, (dp > 0) * 0.3
+    want = np.where(ws + wt > 0, (ws * ds + wt * dp) / np.where(ws + wt > 0, ws + wt, 1), 0.0)
+    assert np.allclose(D, want, rtol=1e-12, atol=1e-14)
+
+
+def test_densify_single_anchor_spreads_a_constant():
+    ds = np.zeros((9, 11)); ds[4, 5] = 2.5
+    z = np.zeros((9, 11))
+    D = DN.densify(ds, z.astype(np.uint8), z, z)
+    assert np.allclose(D, 2.5, rtol=1e-12)
+
+
+def test_densify_contour_splits_and_undetermined_is_missing():
+    ds = np.zeros((6, 10)); ds[2, 1] = 1.0; ds[3, 8] = 4.0
+    B = np.zeros((6, 10), np.uint8); B[:, 5:] = 1          # w = 0 across x = 4 | 5
+    z = np.zeros((6, 10))
+    D = DN.densify(ds, B, z, z)
+    assert np.allclose(D[:, :5], 1.0) and np.allclose(D[:, 5:], 4.0)
+    # pixels cut off from every anchor stay 0: with s = 1 on x >= 5, pairs
+    # inside that band get w = 0 (Eq. 16), while the pairs x = 4 | 5 keep
+    # w = 1 - min(0, 1) = 1, so column 5 joins the anchored left part
+    s = np.zeros((6, 10)); s[:, 5:] = 1.0
+    D2 = DN.densify(np.where(np.arange(10) < 5, ds, 0.0), np.zeros((6, 10), np.uint8), s, np.ones((6, 10)))
+    assert np.allclose(D2[:, :6], 1.0) and (D2[:, 6:] == 0).all()
+
+
+def test_densify_minimises_the_energy_of_eq20():
+    rng = np.random.default_rng(42)
+    ds, B, mf, mi = _dn_inputs(rng, 7, 8, 0.2, contour=True)
+    dp = np.where(rng.random((7, 8)) < 0.2, rng.uniform(1, 3, (7, 8)), 0.0)
+    D = DN.densify(ds, B, mf, mi, dp)
+    e0 = DN.energy(D, ds, B, mf, mi, dp)
+    det = D != 0
+    for k in range(20):
+        v = rng.standard_normal(D.shape) * det
+        for eps in (1e-3, -1e-3):
+            assert DN.energy(D + eps * v, ds, B, mf, mi, dp) > e0
+        # zero directional derivative (central difference of a quadratic is exact)
+        g = (DN.energy(D + 1e-3 * v, ds, B, mf, mi, dp) - DN.energy(D - 1e-3 * v, ds, B, mf, mi, dp)) / 2e-3
+        assert abs(g) < 1e-7 * max(1.0, e0)
