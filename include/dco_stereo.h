@@ -228,6 +228,45 @@ dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *r
                             int16_t *disp_half_out, dco_stream stream);
 
 /*
+ * Depth densification (Sect. 6, Eqs. 13-20): the dense map D minimising
+ *   lambda_d  sum_p w_sparse(p) (D(p) - D_sparse(p))^2
+ * + lambda_s  sum_p sum_{q in N4(p)} w_pq (D(p) - D(q))^2
+ * + lambda_s2 sum_p w_stable(p) (D(p) - D_pre(p))^2
+ * with w_sparse = [D_sparse > 0], w_stable = [D_pre > 0], w_pq = 0 when
+ * exactly one of p, q is on the depth contour, else max(1 - min(s_p, s_q), 0),
+ * s = M_fuse * M_I (Eq. 17); N4 is cut at the border.  Solved on the device
+ * by Jacobi-preconditioned conjugate gradients until the residual of the
+ * normal equations is below tol relative to their right-hand side, or
+ * max_iters; pixels whose smoothness-connected part holds no data stay 0.
+ */
+typedef struct {
+    float lambda_d;   /* 0.80 (Sect. 7.2) */
+    float lambda_s;   /* 1.20 */
+    float lambda_s2;  /* 0.02 */
+    float tol;        /* 1e-5 */
+    int max_iters;    /* 4000 */
+} dco_dense_params;
+
+dco_status dco_dense_params_default(dco_dense_params *p);
+
+/*
+ * d_sparse: device W*H float, 0 = no sparse depth (e.g. dco_stereo_depth's
+ * output).  contour: device W*H bytes, nonzero on the depth contour B_dp, or
+ * NULL (no contour).  m_fuse, m_int: device W*H float, the fused flow
+ * magnitude and the [0, 1]-normalised Canny intensity of Eq. 17, or NULL (0).
+ * d_pre: device W*H float, the previous frame's depth, or NULL (no stability
+ * term).  d_out: device W*H float.  p = NULL uses the defaults.  The call
+ * waits for the solve (it reads a convergence flag between batches of
+ * iterations); dco_stereo_densify_stats gives the iterations run and the
+ * final relative residual.  Needs 36 bytes per pixel of workspace.
+ */
+dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_t *contour, const float *m_fuse,
+                              const float *m_int, const float *d_pre, int W, int H, const dco_dense_params *p,
+                              float *d_out, dco_stream stream);
+
+dco_status dco_stereo_densify_stats(dco_stereo *h, int *iters, double *rel_residual);
+
+/*
  * Stage a7 alone: left-right consistency.  out(x,y) = dl(x,y) if
  * x - dl >= 0 and |dl - dr(x - dl, y)| <= tol, else -1; tol < 0 copies dl.
  * dl, dr, out: device W*H int16.  The handle is only used for its device.

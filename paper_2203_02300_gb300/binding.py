@@ -41,6 +41,20 @@ class Params(ctypes.Structure):
         return p
 
 
+class DenseParams(ctypes.Structure):
+    """dco_dense_params; defaults from dco_dense_params_default()."""
+    _fields_ = [("lambda_d", c_float), ("lambda_s", c_float), ("lambda_s2", c_float), ("tol", c_float),
+                ("max_iters", c_int)]
+
+    @classmethod
+    def default(cls, **over) -> "DenseParams":
+        p = cls()
+        _check(lib().dco_dense_params_default(ctypes.byref(p)), None)
+        for k, v in over.items():
+            setattr(p, k, v)
+        return p
+
+
 class PairDesc(ctypes.Structure):
     _fields_ = [("left", c_void_p), ("right", c_void_p), ("W", c_int), ("H", c_int), ("D", c_int),
                 ("disp_out", c_void_p)]
@@ -86,6 +100,9 @@ def lib():
             "dco_stereo_lr_check": (c_int, [P, P, P, c_int, c_int, c_int, P, P]),
             "dco_stereo_vote": (c_int, [P, P, P, c_int, c_int, c_int, P, P, P]),
             "dco_stereo_downscale": (c_int, [P, P, c_int, c_int, P, P]),
+            "dco_dense_params_default": (c_int, [P]),
+            "dco_stereo_densify": (c_int, [P, P, P, P, P, P, c_int, c_int, P, P, P]),
+            "dco_stereo_densify_stats": (c_int, [P, P, P]),
             "dco_stereo_depth": (c_int, [P, P, P, c_int, c_int, c_int, P, ctypes.c_double, ctypes.c_double, P, P,
                                          P]),
             "dco_stereo_match_batch": (c_int, [P, P, c_int, P, P]),
@@ -266,6 +283,25 @@ class Stereo:
                                      ctypes.byref(params) if params else None, _ptr(out), _stream(stream)),
                self._h)
         return out
+
+    def densify(self, d_sparse, contour=None, m_fuse=None, m_int=None, d_pre=None,
+                params: Optional[DenseParams] = None, out=None, stream=None):
+        """Dense depth (Sect. 6, Eq. 20) from device float maps (H, W); returns
+        the output tensor (the call waits for the solve)."""
+        import torch
+        H, W = d_sparse.shape
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=d_sparse.device)
+        opt = lambda t: _ptr(t) if t is not None else None
+        _check(lib().dco_stereo_densify(self._h, _ptr(d_sparse), opt(contour), opt(m_fuse), opt(m_int),
+                                        opt(d_pre), W, H, ctypes.byref(params) if params else None, _ptr(out),
+                                        _stream(stream)), self._h)
+        return out
+
+    def densify_stats(self) -> tuple[int, float]:
+        it, rr = c_int(0), ctypes.c_double(0.0)
+        _check(lib().dco_stereo_densify_stats(self._h, ctypes.byref(it), ctypes.byref(rr)), self._h)
+        return it.value, rr.value
 
     def downscale(self, img, stream=None):
         import torch

@@ -976,6 +976,10 @@ struct dco_stereo {
     std::vector<cudaEvent_t> pool;
     std::vector<ProfAgg> agg;
     std::string last_error;
+    int *dn_pin = nullptr;                   // pinned convergence flags of the densify solve
+    cudaEvent_t dn_ev[2] = {nullptr, nullptr};
+    int dn_iters = 0;
+    double dn_relres = 0.0;
 };
 
 namespace {
@@ -1492,6 +1496,8 @@ dco_status run_match(dco_stereo *h, const uint8_t *left, const uint8_t *right, i
 } // namespace
 
 // ===================================================================== C ABI
+#include "densify.cuh"
+
 extern "C" {
 
 dco_status dco_params_default(dco_params *p)
@@ -1563,6 +1569,9 @@ void dco_stereo_destroy(dco_stereo *h)
     cudaFree(h->d_tables);
     cudaFree(h->stage);
     if (h->h_tables) cudaFreeHost(h->h_tables);
+    if (h->dn_pin) cudaFreeHost(h->dn_pin);
+    for (auto e : h->dn_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -1773,6 +1782,112 @@ dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint
     if (!left || !right || !vol_out || (view != 0 && view != 1) || !dims_valid(W, H, D)) return DCO_EINVAL;
     return run_match(h, left, right, W, H, D, p, nullptr, nullptr, nullptr, nullptr, nullptr, vol_out, view,
                      (cudaStream_t)stream);
+}
+
+dco_status dco_dense_params_default(dco_dense_params *p)
+{
+    if (!p) return DCO_EINVAL;
+    p->lambda_d = 0.80f;    // Sect. 7.2
+    p->lambda_s = 1.20f;
+    p->lambda_s2 = 0.02f;
+    p->tol = 1e-5f;
+    p->max_iters = 4000;
+    return DCO_OK;
+}
+
+dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_t *contour, const float *m_fuse,
+                              const float *m_int, const float *d_pre, int W, int H, const dco_dense_params *pin,
+                              float *d_out, dco_stream stream)
+{
+    if (!h || !d_sparse || !d_out || W < 1 || H < 1 || W > 32768 || H > 32768) return DCO_EINVAL;
+    dco_dense_params p;
+    if (pin) p = *pin;
+    else dco_dense_params_default(&p);
+    if (!(p.lambda_d >= 0.f) || !(p.lambda_s >= 0.f) || !(p.lambda_s2 >= 0.f) || !(p.tol > 0.f) ||
+        p.max_iters < 0 || p.max_iters > 1000000)
+        return DCO_EINVAL;
+    DCO_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)W * H;
+    const int nblk = (int)((n + kDnBlock - 1) / kDnBlock);
+    // workspace: r, z, p0, p1, Ap, wr, wd, diag, b; block partials; scalars
+    const size_t fl = align_up(4 * n);
+    const size_t off_part = 9 * fl, off_sc = off_part + align_up(16 * (size_t)nblk);
+    dco_status st = ensure_ws(h, off_sc + align_up(sizeof(DnScalars)));
+    if (st != DCO_OK) return st;
+    if (!h->dn_pin) {
+        DCO_CUDA(h, cudaMallocHost((void **)&h->dn_pin, 2 * sizeof(int)));
+        for (auto &e : h->dn_ev) DCO_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    DnArgs a{};
+    a.ds = d_sparse; a.dpre = d_pre; a.mf = m_fuse; a.mi = m_int; a.contour = contour;
+    float *f = ws_ptr<float>(h, 0);
+    auto arr = [&](int k) { return reinterpret_cast<float *>(reinterpret_cast<char *>(f) + k * fl); };
+    a.x = d_out; a.r = arr(0); a.z = arr(1); a.p[0] = arr(2); a.p[1] = arr(3); a.ap = arr(4);
+    a.wr = arr(5); a.wd = arr(6); a.dg = arr(7); a.b = arr(8);
+    a.part = ws_ptr<double>(h, off_part);
+    a.sc = ws_ptr<DnScalars>(h, off_sc);
+    a.W = W; a.H = H; a.nblk = nblk;
+    a.lambda_d = p.lambda_d; a.lambda_s = p.lambda_s; a.lambda_s2 = p.lambda_s2;
+    a.tol2 = (double)p.tol * p.tol;
+    {
+        ProfScope ps(h, s, "k_dn_setup");
+        k_dn_setup<<<nblk, kDnBlock, 0, s>>>(a);
+    }
+    {
+        ProfScope ps(h, s, "k_dn_init");
+        k_dn_init<<<nblk, kDnBlock, 0, s>>>(a);
+    }
+    k_dn_red<<<1, 1024, 0, s>>>(a, 0);
+    DCO_CUDA(h, cudaGetLastError());
+    // iterations in batches; the host looks at the flag of the batch before
+    // the last one, so the device keeps one batch queued ahead
+    constexpr int kBatch = 16;
+    int it = 0, nb = 0;
+    bool stop = false;
+    while (it < p.max_iters && !stop) {
+        const int m = std::min(kBatch, p.max_iters - it);
+        for (int k = 0; k < m; k++, it++) {
+            {
+                ProfScope ps(h, s, "k_dn_ap");
+                k_dn_ap<<<nblk, kDnBlock, 0, s>>>(a, it);
+            }
+            k_dn_red<<<1, 1024, 0, s>>>(a, 1);
+            {
+                ProfScope ps(h, s, "k_dn_upd");
+                k_dn_upd<<<nblk, kDnBlock, 0, s>>>(a, it);
+            }
+            k_dn_red<<<1, 1024, 0, s>>>(a, 2);
+        }
+        {
+            ProfScope ps(h, s, "k_dn_resid");
+            k_dn_resid<<<nblk, kDnBlock, 0, s>>>(a);
+        }
+        k_dn_red<<<1, 1024, 0, s>>>(a, 3);
+        DCO_CUDA(h, cudaGetLastError());
+        const int slot = nb & 1;
+        DCO_CUDA(h, cudaMemcpyAsync(h->dn_pin + slot, &a.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DCO_CUDA(h, cudaEventRecord(h->dn_ev[slot], s));
+        if (nb > 0) {
+            DCO_CUDA(h, cudaEventSynchronize(h->dn_ev[slot ^ 1]));
+            stop = h->dn_pin[slot ^ 1] != 0;
+        }
+        nb++;
+    }
+    DnScalars sc{};
+    DCO_CUDA(h, cudaMemcpyAsync(&sc, a.sc, sizeof sc, cudaMemcpyDeviceToHost, s));
+    DCO_CUDA(h, cudaStreamSynchronize(s));
+    h->dn_iters = sc.iters;
+    h->dn_relres = sc.bb > 0.0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+    return DCO_OK;
+}
+
+dco_status dco_stereo_densify_stats(dco_stereo *h, int *iters, double *rel_residual)
+{
+    if (!h) return DCO_EINVAL;
+    if (iters) *iters = h->dn_iters;
+    if (rel_residual) *rel_residual = h->dn_relres;
+    return DCO_OK;
 }
 
 dco_status dco_stereo_lr_check(dco_stereo *h, const int16_t *dl, const int16_t *dr, int W, int H, int tol,
