@@ -276,6 +276,7 @@ def own_arm(args):
         extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
         extras["smooth_config2"] = smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        extras["densify_1280x720"] = densify_full_size(torch, binding, st, flush, dev)
         extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
         extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
         extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
@@ -408,6 +409,64 @@ def smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 
     return {"ms_path": round(t0, 4), "ms_path_smoothed": round(t1, 4),
             "k_smooth": {"launches_per_frame": n / reps, "avg_us": round(avg, 3) if avg else None,
                          "frac_hbm": round(alg / (avg * 1e-6) / 1e9 / pk["hbm_gbs"], 4) if avg else None}}
+
+
+# --------------------------------------------- densification (Sect. 6)
+def densify_full_size(torch, binding, st, flush, dev, W: int = 1280, H: int = 720, reps: int = 5):
+    """Eq. 20 on a 1280x720 frame: the sparse depth of the quarter-size path,
+    a depth contour where the ground truth jumps, texture weights from the
+    image gradient (M_fuse = 1).  Median time per solve, iterations, and the
+    two streaming kernels against their algorithmic bytes."""
+    import numpy as np
+    from paper_2203_02300_gb300 import scenes
+    s = scenes.plane_scene(W, H, 128, 12, seed=scenes.seed_for(2, 950), drange=(4, 120), slanted=True,
+                           noise_sigma=2.0)
+    L = torch.from_numpy(s.left).to(dev)
+    R = torch.from_numpy(s.right).to(dev)
+    z = st.depth(L, R, 64, 700.0, 0.12)
+    g = s.disp
+    B = ((np.abs(np.diff(g, axis=1, append=g[:, -1:])) > 1) | (np.abs(np.diff(g, axis=0, append=g[-1:])) > 1))
+    Y = s.left.astype(np.float32).mean(axis=2)
+    gm = np.hypot(*np.gradient(Y))
+    Bd = torch.from_numpy(B.astype(np.uint8)).to(dev)
+    mi = torch.from_numpy((gm / gm.max()).astype(np.float32)).to(dev)
+    mf = torch.ones_like(mi)
+    out = torch.empty_like(z)
+    p = binding.DenseParams.default()
+    stream = torch.cuda.current_stream(dev)
+    st.densify(z, Bd, mf, mi, None, p, out=out)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.densify(z, Bd, mf, mi, None, p, out=out)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    iters, rel = st.densify_stats()
+    st.set_profiling(True)
+    st.profile_reset()
+    st.densify(z, Bd, mf, mi, None, p, out=out)
+    torch.cuda.synchronize(dev)
+    prof = st.profile()
+    st.set_profiling(False)
+    pk, _ = peaks()
+    n = W * H
+    alg = {"k_dn_ap": 4 * n * 7, "k_dn_upd": 4 * n * 8}   # ap: z, p, wr, wd, diag in; p, Ap out. upd: x, p, r, Ap, diag in; x, r, z out
+    kern = {}
+    for k, (cnt, ms) in prof.items():
+        avg = ms / cnt * 1e3
+        e = {"launches": cnt, "avg_us": round(avg, 3)}
+        if k in alg:
+            gbs = alg[k] / (avg * 1e-6) / 1e9
+            e.update(achieved_gbs=round(gbs, 1), frac_hbm=round(gbs / pk["hbm_gbs"], 4))
+        kern[k] = e
+    med = statistics.median(ts)
+    return {"size": f"{W}x{H}", "sparse_fraction": float((z > 0).float().mean().item()),
+            "iterations": iters, "rel_residual": rel, "tol": float(p.tol), "ms_per_solve": round(med, 3),
+            "us_per_iteration": round(1e3 * med / max(iters, 1), 2), "kernels": kern}
 
 
 # ------------------------------------------- quarter size + depth (Sect. 4.4)

@@ -976,8 +976,11 @@ struct dco_stereo {
     std::vector<cudaEvent_t> pool;
     std::vector<ProfAgg> agg;
     std::string last_error;
-    int *dn_pin = nullptr;                   // pinned convergence flags of the densify solve
+    int *dn_pin = nullptr;                   // pinned convergence flag of the densify solve
     cudaEvent_t dn_ev[2] = {nullptr, nullptr};
+    cudaStream_t dn_stream = nullptr;        // private stream the iteration batch is captured on
+    cudaGraphExec_t dn_exec = nullptr;       // one captured batch of iterations
+    std::vector<unsigned char> dn_key;       // the arguments it was captured with
     int dn_iters = 0;
     double dn_relres = 0.0;
 };
@@ -1033,8 +1036,11 @@ struct ProfScope {
     dco_stereo *h;
     cudaStream_t s;
     ProfEvent ev{};
-    ProfScope(dco_stereo *h_, cudaStream_t s_, const char *name) : h(h_), s(s_)
+    // name == nullptr: a launch being captured into a graph (counted when the
+    // graph runs, never timed)
+    ProfScope(dco_stereo *h_, cudaStream_t s_, const char *name) : h(name ? h_ : nullptr), s(s_)
     {
+        if (!h) return;
         h->launches++;
         if (h->profiling) {
             ev.name = name;
@@ -1045,7 +1051,7 @@ struct ProfScope {
     }
     ~ProfScope()
     {
-        if (h->profiling) {
+        if (h && h->profiling) {
             cudaEventRecord(ev.b, s);
             h->pending.push_back(ev);
         }
@@ -1570,6 +1576,8 @@ void dco_stereo_destroy(dco_stereo *h)
     cudaFree(h->stage);
     if (h->h_tables) cudaFreeHost(h->h_tables);
     if (h->dn_pin) cudaFreeHost(h->dn_pin);
+    if (h->dn_exec) cudaGraphExecDestroy(h->dn_exec);
+    if (h->dn_stream) cudaStreamDestroy(h->dn_stream);
     for (auto e : h->dn_ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -1799,7 +1807,7 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
                               const float *m_int, const float *d_pre, int W, int H, const dco_dense_params *pin,
                               float *d_out, dco_stream stream)
 {
-    if (!h || !d_sparse || !d_out || W < 1 || H < 1 || W > 32768 || H > 32768) return DCO_EINVAL;
+    if (!h || !d_sparse || !d_out || W < 1 || H < 1 || W > 32768 || H > 32768) return DCO_EINVAL;   // W*H < 2^31
     dco_dense_params p;
     if (pin) p = *pin;
     else dco_dense_params_default(&p);
@@ -1808,8 +1816,17 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
         return DCO_EINVAL;
     DCO_CUDA(h, cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DCO_CUDA(h, cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        h->last_error = "dco_stereo_densify waits for its solve and cannot be captured";
+        return DCO_EINVAL;
+    }
     const size_t n = (size_t)W * H;
-    const int nblk = (int)((n + kDnBlock - 1) / kDnBlock);
+    // grid-stride kernels: at most 8 resident blocks per multiprocessor
+    int nsm = 0;
+    DCO_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int nblk = (int)std::min<size_t>((n + kDnBlock - 1) / kDnBlock, (size_t)std::max(nsm, 1) * 8);
     // workspace: r, z, p0, p1, Ap, wr, wd, diag, b; block partials; scalars
     const size_t fl = align_up(4 * n);
     const size_t off_part = 9 * fl, off_sc = off_part + align_up(16 * (size_t)nblk);
@@ -1819,7 +1836,8 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
         DCO_CUDA(h, cudaMallocHost((void **)&h->dn_pin, 2 * sizeof(int)));
         for (auto &e : h->dn_ev) DCO_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    DnArgs a{};
+    DnArgs a;
+    std::memset(&a, 0, sizeof a);   // padding included: the bytes key the captured graph
     a.ds = d_sparse; a.dpre = d_pre; a.mf = m_fuse; a.mi = m_int; a.contour = contour;
     float *f = ws_ptr<float>(h, 0);
     auto arr = [&](int k) { return reinterpret_cast<float *>(reinterpret_cast<char *>(f) + k * fl); };
@@ -1838,39 +1856,71 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
         ProfScope ps(h, s, "k_dn_init");
         k_dn_init<<<nblk, kDnBlock, 0, s>>>(a);
     }
-    k_dn_red<<<1, 1024, 0, s>>>(a, 0);
     DCO_CUDA(h, cudaGetLastError());
-    // iterations in batches; the host looks at the flag of the batch before
-    // the last one, so the device keeps one batch queued ahead
-    constexpr int kBatch = 16;
+    // Iterations run in batches of kDnIters, each closed by the residual
+    // replacement, the true-residual test and a copy of the (sticky) done
+    // flag to pinned memory.  A batch is one CUDA graph launch (captured once
+    // per argument set on a private stream; per-kernel profiling uses plain
+    // launches instead); the host keeps one batch queued ahead and stops
+    // enqueuing once the flag of an earlier batch reads 1.
+    constexpr int kDnIters = 16;   // even: buffer parity repeats per batch
+    auto enqueue = [&](cudaStream_t q, int it0, int m, bool prof) -> cudaError_t {
+        for (int k = 0; k < m; k++) {
+            const int it = it0 + k;
+            {
+                ProfScope ps(h, q, prof ? "k_dn_ap" : nullptr);
+                k_dn_ap<<<nblk, kDnBlock, 0, q>>>(a, it);
+            }
+            {
+                ProfScope ps(h, q, prof ? "k_dn_upd" : nullptr);
+                k_dn_upd<<<nblk, kDnBlock, 0, q>>>(a, it);
+            }
+        }
+        {
+            ProfScope ps(h, q, prof ? "k_dn_resid" : nullptr);
+            k_dn_resid<<<nblk, kDnBlock, 0, q>>>(a);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->dn_pin, &a.sc->done, sizeof(int), cudaMemcpyDeviceToHost, q);
+        return e;
+    };
+    const bool graph = !h->profiling;
+    if (graph) {
+        const unsigned char *ka = reinterpret_cast<const unsigned char *>(&a);
+        if (!h->dn_exec || h->dn_key.size() != sizeof a || std::memcmp(h->dn_key.data(), ka, sizeof a)) {
+            if (h->dn_exec) {
+                cudaGraphExecDestroy(h->dn_exec);
+                h->dn_exec = nullptr;
+            }
+            if (!h->dn_stream) DCO_CUDA(h, cudaStreamCreateWithFlags(&h->dn_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            DCO_CUDA(h, cudaStreamBeginCapture(h->dn_stream, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e = enqueue(h->dn_stream, 0, kDnIters, false);
+            const cudaError_t e2 = cudaStreamEndCapture(h->dn_stream, &g);
+            DCO_CUDA(h, e);
+            DCO_CUDA(h, e2);
+            const cudaError_t e3 = cudaGraphInstantiate(&h->dn_exec, g, 0);
+            cudaGraphDestroy(g);
+            DCO_CUDA(h, e3);
+            h->dn_key.assign(ka, ka + sizeof a);
+        }
+    }
+    *h->dn_pin = 0;
     int it = 0, nb = 0;
     bool stop = false;
     while (it < p.max_iters && !stop) {
-        const int m = std::min(kBatch, p.max_iters - it);
-        for (int k = 0; k < m; k++, it++) {
-            {
-                ProfScope ps(h, s, "k_dn_ap");
-                k_dn_ap<<<nblk, kDnBlock, 0, s>>>(a, it);
-            }
-            k_dn_red<<<1, 1024, 0, s>>>(a, 1);
-            {
-                ProfScope ps(h, s, "k_dn_upd");
-                k_dn_upd<<<nblk, kDnBlock, 0, s>>>(a, it);
-            }
-            k_dn_red<<<1, 1024, 0, s>>>(a, 2);
+        const int m = std::min(kDnIters, p.max_iters - it);
+        if (graph && m == kDnIters) {
+            DCO_CUDA(h, cudaGraphLaunch(h->dn_exec, s));
+            h->launches += 2 * kDnIters + 1;
+        } else {
+            DCO_CUDA(h, enqueue(s, it, m, true));
         }
-        {
-            ProfScope ps(h, s, "k_dn_resid");
-            k_dn_resid<<<nblk, kDnBlock, 0, s>>>(a);
-        }
-        k_dn_red<<<1, 1024, 0, s>>>(a, 3);
-        DCO_CUDA(h, cudaGetLastError());
-        const int slot = nb & 1;
-        DCO_CUDA(h, cudaMemcpyAsync(h->dn_pin + slot, &a.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-        DCO_CUDA(h, cudaEventRecord(h->dn_ev[slot], s));
+        it += m;
+        DCO_CUDA(h, cudaEventRecord(h->dn_ev[nb & 1], s));
         if (nb > 0) {
-            DCO_CUDA(h, cudaEventSynchronize(h->dn_ev[slot ^ 1]));
-            stop = h->dn_pin[slot ^ 1] != 0;
+            DCO_CUDA(h, cudaEventSynchronize(h->dn_ev[(nb - 1) & 1]));
+            stop = *reinterpret_cast<volatile int *>(h->dn_pin) != 0;
         }
         nb++;
     }
