@@ -42,6 +42,25 @@ __device__ __forceinline__ uint32_t grey_of(uint32_t c)
     return (77u * (c & 0xffu) + 150u * ((c >> 8) & 0xffu) + 29u * ((c >> 16) & 0xffu) + 128u) >> 8;
 }
 
+// Colour r | g<<8 | b<<16 spread into three 10-bit fields r | g<<10 | b<<20.
+// With K holding tau - 1 + 512 in every field, (E(c) + K - E(p)) keeps each
+// field in [1, 1023] (no carry or borrow between fields) and has the field's
+// bit 9 set exactly when c_i - p_i + tau - 1 >= 0; the same with c and p
+// swapped gives the other side, so every channel has |c_i - p_i| < tau
+// exactly when all six bit-9s are set.
+constexpr uint32_t kM9 = (1u << 9) | (1u << 19) | (1u << 29);
+__device__ __forceinline__ uint32_t spread10(uint32_t c)
+{
+    return (c & 0xffu) | ((c & 0xff00u) << 2) | ((c & 0xff0000u) << 4);
+}
+// back to bytes r | g<<8 | b<<16
+__device__ __forceinline__ uint32_t unspread10(uint32_t e)
+{
+    return (e & 0xffu) | ((e >> 2) & 0xff00u) | ((e >> 4) & 0xff0000u);
+}
+
+// k_pack stores every colour spread (the arm walks read each candidate many
+// times; the record keeps the bytes)
 __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   // pixels 4q .. 4q+3
 {
     const int i0 = 4 * q;
@@ -65,12 +84,12 @@ __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   /
         }
     }
     if (i0 + 4 <= a.npx) {
-        *reinterpret_cast<uint4 *>(rgbx + i0) = make_uint4(c[0], c[1], c[2], c[3]);
+        *reinterpret_cast<uint4 *>(rgbx + i0) = make_uint4(spread10(c[0]), spread10(c[1]), spread10(c[2]), spread10(c[3]));
         *reinterpret_cast<uint32_t *>(grey + i0) =
             grey_of(c[0]) | (grey_of(c[1]) << 8) | (grey_of(c[2]) << 16) | (grey_of(c[3]) << 24);
     } else {
         for (int k = 0; i0 + k < a.npx; k++) {
-            rgbx[i0 + k] = c[k];
+            rgbx[i0 + k] = spread10(c[k]);
             grey[i0 + k] = (uint8_t)grey_of(c[k]);
         }
     }
@@ -86,17 +105,6 @@ constexpr int kTX = 32, kTY = 8;
 constexpr int kMaxCW = 15, kMaxCH = 15;
 constexpr int kGW = 48;   // grey tile row pitch (>= kTX + kMaxCW - 1, multiple of 4)
 
-// Colour r | g<<8 | b<<16 spread into three 10-bit fields r | g<<10 | b<<20.
-// With K holding tau - 1 + 512 in every field, (E(c) + K - E(p)) keeps each
-// field in [1, 1023] (no carry or borrow between fields) and has the field's
-// bit 9 set exactly when c_i - p_i + tau - 1 >= 0; the same with c and p
-// swapped gives the other side, so every channel has |c_i - p_i| < tau
-// exactly when all six bit-9s are set.
-constexpr uint32_t kM9 = (1u << 9) | (1u << 19) | (1u << 29);
-__device__ __forceinline__ uint32_t spread10(uint32_t c)
-{
-    return (c & 0xffu) | ((c & 0xff00u) << 2) | ((c & 0xff0000u) << 4);
-}
 // all channels within tau of p, given Kp = K - E(p) and pK = E(p) + K
 __device__ __forceinline__ bool within(uint32_t ec, uint32_t Kp, uint32_t pK)
 {
@@ -182,12 +190,11 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     const bool use1 = a.tau1 < 256, use2 = a.tau2 < 256;
     const uint32_t k1 = 0x00100401u * (uint32_t)(min(a.tau1, 255) + 511);   // tau - 1 + 512 per field
     const uint32_t k2 = 0x00100401u * (uint32_t)(min(a.tau2, 255) + 511);
-    const uint32_t ep = spread10(p);
+    const uint32_t ep = p;   // colours are stored spread (k_pack)
     const uint32_t K1p = k1 - ep, pK1 = ep + k1, K2p = k2 - ep, pK2 = ep + k2;
     // step j fails: far from p or from its predecessor (tau1), or beyond L2
     // and far from p (tau2)
-    auto fails = [&](uint32_t c, uint32_t prev, int j) -> bool {
-        const uint32_t ec = spread10(c), eq = spread10(prev);
+    auto fails = [&](uint32_t ec, uint32_t eq, int j) -> bool {
         if (use1 && (!within(ec, K1p, pK1) || !within(ec, k1 - eq, eq + k1))) return true;
         return j > L2 && use2 && !within(ec, K2p, pK2);
     };
@@ -234,7 +241,7 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     const int lmin = min(min(arm[0], arm[1]), min(arm[2], arm[3]));
     const float alphaS = __ldg(a.tables + kTabAD + kTabCen + lmin);
     (img ? a.rec[1] : a.rec[0])[(size_t)y * a.rpitch + x] =
-        make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), p | (uint32_t(lmin) << 24), __float_as_uint(alphaS));
+        make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), unspread10(p) | (uint32_t(lmin) << 24), __float_as_uint(alphaS));
     (img ? a.arms[1] : a.arms[0])[i] = make_uchar4((uint8_t)arm[0], (uint8_t)arm[1], (uint8_t)arm[2], (uint8_t)arm[3]);
 }
 
@@ -547,6 +554,23 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     const int ng = (a.dc + 31) / 32;
     const bool want_vol = a.vol != nullptr && view == a.vol_view;
 
+    // one 64-bit base per group, 32-bit row offsets (31 * W * dstride < 2^32
+    // for W <= 16384, D <= 256); full segments need no predicates
+    uint32_t v[kVSeg];
+    auto load = [&](int g) {
+        const uint32_t *src = sh + (size_t)(ya + sa) * rowstride + g * 32;
+        const uint32_t rs = (uint32_t)rowstride;
+        uint32_t off = 0;
+        if (full) {
+#pragma unroll
+            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = __ldg(src + off);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = sa + u < sb ? __ldg(src + off) : 0u;
+        }
+    };
+    load(0);   // the first group's rows are in flight during the arm-word work
+
     // arm word of this lane's row and the region-size prefix (d independent)
     const int r = sa + lane;
     const bool rin = r < sb;
@@ -567,20 +591,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
 
     for (int g = 0; g < ng; g++) {
         // ---- A: this warp's 32 rows of the slice column, lane = disparity
-        // one 64-bit base per group, 32-bit row offsets (31 * W * dstride
-        // < 2^32 for W <= 16384, D <= 256); full segments need no predicates
-        uint32_t v[kVSeg];
-        const uint32_t *src = sh + (size_t)(ya + sa) * rowstride + g * 32;
-        const uint32_t rs = (uint32_t)rowstride;
-        if (full) {
-            uint32_t off = 0;
-#pragma unroll
-            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = __ldg(src + off);
-        } else {
-            uint32_t off = 0;
-#pragma unroll
-            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = sa + u < sb ? __ldg(src + off) : 0u;
-        }
+        if (g > 0) load(g);
         uint32_t tot = 0;
 #pragma unroll
         for (int u = 0; u < kVSeg; u++) tot += v[u];

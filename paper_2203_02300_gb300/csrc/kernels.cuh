@@ -1,7 +1,7 @@
 // Device-side types and constants of the AD-census matcher (arXiv 2203.02300, Sect. 4).
 //
 // Data layout in HBM (row-major, pixel index i = y*W + x):
-//   rgbx[i]  uint32 r | g<<8 | b<<16           packed colour of the input image
+//   rgbx[i]  uint32 r | g<<10 | b<<20          colour in three 10-bit fields (arm tests)
 //   grey[i]  uint8  (77R + 150G + 29B + 128) >> 8
 //   rec[y*rpitch + x]  uint4 {census bits 0-31, census bits 32-63,
 //                    r | g<<8 | b<<16 | Lmin<<24, float bits of alpha(Lmin)*S}
