@@ -270,6 +270,15 @@ def own_arm(args):
             "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
             if src == "measured" else "fallback 6.8 TB/s"}
 
+    # ---- cost + aggregation against a staged design: a staged path streams
+    # 16 B per view-evaluation (cost write, H read and write, V read); this one
+    # 8 B (H writes the horizontal sums, V reads them)
+    evals = 2 * npx * D
+    hv_us = sum(kernels[k]["avg_us"] * kernels[k]["launches"] for k in ("k_hagg", "k_vagg") if k in kernels) / args.steps
+    staged = {"ours_h_plus_v_us": round(hv_us, 2), "ours_bytes_per_eval": 8, "staged_bytes_per_eval": 16,
+              "ours_bytes_at_hbm_peak_us": round(8 * evals / (pk["hbm_gbs"] * 1e3), 2),
+              "staged_bytes_at_hbm_peak_us": round(16 * evals / (pk["hbm_gbs"] * 1e3), 2)}
+
     # ---- config 3 (batched) and config 4 (serving), rank 0 only
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -301,6 +310,7 @@ def own_arm(args):
                     "latency_ms": {"p50": statistics.median(e2e_ms),
                                    "p99": sorted(e2e_ms)[min(len(e2e_ms) - 1, int(0.99 * len(e2e_ms)))]}},
             "roofline": roof,
+            "cost_aggregation_vs_staged": staged,
             "kernels": kernels,
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
