@@ -281,7 +281,7 @@ __device__ __forceinline__ void smooth_body(const SmoothArgs &a, int i, int img)
 // the tables, the reference records of the prefix range [xa, xb) (the
 // output columns plus an L1 reach on both sides), the candidate records of
 // the group and the output columns' arms into shared memory.  Then:
-//   A. each warp walks a segment of kHSeg columns: Eq. 1 cost rounded to
+//   A. each warp walks a segment of kHSegCost columns: Eq. 1 cost rounded to
 //      fixed point, local inclusive prefix into P[x - xa][lane];
 //   B. segment totals -> exclusive offsets, added to P in place;
 //   C. every output column xo: S_H = P(xo + r) - P(xo - l - 1) (the
@@ -417,7 +417,7 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     const uint32_t Sint = a.Sint;
 
     // ---- A: costs and local prefix of this warp's segment
-    const int sa = warp * kHSeg, sb = min(len, sa + kHSeg);   // relative to xa
+    const int sa = warp * kHSegCost, sb = min(len, sa + kHSegCost);   // relative to xa
     uint32_t run = 0;
     auto cost_at = [&](const uint4 pr, const uint4 po, int x) -> uint32_t {
         const int h = __popc(pr.x ^ po.x) + __popc(pr.y ^ po.y);
@@ -785,8 +785,9 @@ __global__ void __launch_bounds__(kTX * kTY) k_prep(const __grid_constant__ Batc
     prep_body<CW, CH>(b.p[i], bx, by, bz);
 }
 
-template <int N>
-__global__ void __launch_bounds__(16 * 32) k_hagg(const __grid_constant__ Batch<HArgs, N> b)
+// kWide: blocks of more than kHNarrow warps (rows wider than 640 columns)
+template <int N, bool kWide>
+__global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __grid_constant__ Batch<HArgs, N> b)
 {
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
@@ -938,7 +939,7 @@ HGeom hagg_geom(int W, int H, int dc, int L1)
     HGeom g{};
     g.chunk = W <= kHMaxLen ? W : 512;
     const int len = std::min(W, g.chunk + 2 * L1);
-    g.nw = (len + kHSeg - 1) / kHSeg;
+    g.nw = (len + kHSegCost - 1) / kHSegCost;
     g.smem = HSmem(len, g.chunk, g.nw).total;
     const int ngroups = (dc + 31) / 32;
     g.grid = dim3((W + g.chunk - 1) / g.chunk, H, 2 * ngroups);
@@ -1350,8 +1351,11 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         vb[vg.nw].push_back(b);
     }
     for (auto &kv : hb) {
-        dco_status st = launch_items(h, s, "k_hagg", k_hagg<1>, k_hagg<kBatchMax>, kv.second, kv.first * 32,
-                                     hsm[kv.first]);
+        dco_status st = kv.first <= kHNarrow
+                            ? launch_items(h, s, "k_hagg", k_hagg<1, false>, k_hagg<kBatchMax, false>, kv.second,
+                                           kv.first * 32, hsm[kv.first])
+                            : launch_items(h, s, "k_hagg", k_hagg<1, true>, k_hagg<kBatchMax, true>, kv.second,
+                                           kv.first * 32, hsm[kv.first]);
         if (st != DCO_OK) return st;
     }
     for (auto &kv : vb) {
@@ -1382,7 +1386,8 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
         const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
         const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
         const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
-        hsm[hg.nw] = std::max(hsm[hg.nw], (size_t)HVSmem(hlen, hg.chunk, hg.nw).total);
+        const int hnw = (hlen + kHSeg - 1) / kHSeg;   // the vote pass walks 64-column segments
+        hsm[hnw] = std::max(hsm[hnw], (size_t)HVSmem(hlen, hg.chunk, hnw).total);
         vsm[vg.nw] = std::max(vsm[vg.nw], vagg_smem_words(vlen, vg.nw) * 4);
         Item<HVArgs> a{};
         a.a.disp = j.vsrc;
@@ -1391,7 +1396,7 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
         a.a.W = j.W; a.a.H = j.H; a.a.d0 = d0; a.a.dstride = j.L.dstride;
         a.a.L1 = dv.L1; a.a.chunk = hg.chunk;
         a.gx = hg.grid.x; a.gy = hg.grid.y; a.gz = (dc + 31) / 32;
-        hb[hg.nw].push_back(a);
+        hb[hnw].push_back(a);
         Item<VArgs> b{};
         for (int v = 0; v < 2; v++) {
             b.a.sh[v] = a.a.sh;

@@ -34,9 +34,12 @@ constexpr int kTabFloats = kTabAD + kTabCen + kTabAlpha;
 // discarded: the cost of a match outside the image is 1).
 constexpr int kRPad = 256;
 
-// The H pass scans columns in warp segments of kHSeg, the V pass rows in
-// segments of 1 << seglog (powers of two: segment index = shift).
+// The cost H pass scans columns in warp segments of kHSegCost (one chunk per
+// row up to kHMaxLen columns, else 512-column chunks), the vote H pass in
+// segments of kHSeg; the V pass rows in segments of 1 << seglog.
 constexpr int kHSegLog = 6, kHSeg = 1 << kHSegLog;
+constexpr int kHSegCost = 32;
+constexpr int kHNarrow = 20;     // warps of the cost H instantiation kept at two blocks per SM
 constexpr int kHMaxLen = 1024;   // prefix columns one H block holds
 constexpr int kVMaxLen = 1024;   // prefix rows one V block holds
 
