@@ -153,10 +153,12 @@ dco_status dco_stereo_match_views(dco_stereo *h, const uint8_t *left, const uint
                                   float *cost_left, float *cost_right, dco_stream stream);
 
 /*
- * As dco_stereo_match, with host buffers: copies left/right (host, W*H*3
- * bytes each) to the handle's device staging buffers, runs the path, copies
- * the disparity map back into disp_host (host, W*H int16) and waits for the
- * stream.  Pinned host memory makes the copies asynchronous.
+ * As dco_stereo_match, with host buffers left/right (W*H*3 bytes each) and
+ * disp_host (W*H int16); waits for the stream before returning.  When all
+ * three are device-accessible (pinned, registered or managed host memory,
+ * reached over NVLink-C2C on Grace systems) and p->vote_iters is 0, the
+ * kernels read the images and write the map in place; otherwise the images
+ * are copied to the handle's device staging buffers and the map back.
  */
 dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host,
                                  const uint8_t *right_host, int W, int H, int D,

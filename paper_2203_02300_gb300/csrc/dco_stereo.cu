@@ -1638,6 +1638,18 @@ dco_status dco_stereo_match(dco_stereo *h, const uint8_t *left, const uint8_t *r
                                   stream);
 }
 
+// the device can dereference p at the same address (pinned, registered or
+// managed host memory)
+static bool device_accessible(const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // plain pageable memory: not an error for the caller
+        return false;
+    }
+    return (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged) && at.devicePointer == p;
+}
+
 dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host, const uint8_t *right_host, int W,
                                  int H, int D, const dco_params *pin, int16_t *disp_host, dco_stream stream)
 {
@@ -1648,6 +1660,19 @@ dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host, const 
     const size_t img = (size_t)W * H * 3, out = (size_t)W * H * 2;
     const size_t need = align_up(img) * 2 + align_up(out);
     cudaStream_t s = (cudaStream_t)stream;
+    // Buffers the device can dereference (pinned, registered or managed host
+    // memory; over NVLink-C2C on Grace systems) are read by k_pack and
+    // written by the consistency check in place, without staging copies.
+    // With Eq. 4 rounds the map is rewritten several times: it stays on the
+    // device and is copied once.
+    if (device_accessible(left_host) && device_accessible(right_host) && device_accessible(disp_host) &&
+        p.vote_iters == 0) {
+        st = run_match(h, left_host, right_host, W, H, D, p, disp_host, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       0, s);
+        if (st != DCO_OK) return st;
+        DCO_CUDA(h, cudaStreamSynchronize(s));
+        return DCO_OK;
+    }
     if (h->stage_cap < need) {
         if (h->stage) {
             DCO_CUDA(h, cudaDeviceSynchronize());

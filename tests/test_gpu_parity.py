@@ -197,11 +197,19 @@ def test_config5_sampled_rows(env):
 
 
 def test_match_host_equals_device_path(env):
+    # pageable buffers (staging copies), pinned buffers (read and written in
+    # place by the kernels) and pinned buffers with Eq. 4 rounds (staged map)
     torch, binding, st = env
     s = scenes.config_scene(2)
     out = st.match(dev(torch, s.left), dev(torch, s.right), s.D).cpu().numpy()
-    host = st.match_host(s.left, s.right, s.D)
-    assert np.array_equal(out, host)
+    assert np.array_equal(out, st.match_host(s.left, s.right, s.D))
+    Lp = torch.from_numpy(s.left).pin_memory().numpy()
+    Rp = torch.from_numpy(s.right).pin_memory().numpy()
+    op = torch.full((s.H, s.W), -7, dtype=torch.int16).pin_memory().numpy()
+    assert np.array_equal(out, st.match_host(Lp, Rp, s.D, out=op))
+    pv = binding.Params.default(vote_iters=1)
+    want = st.match(dev(torch, s.left), dev(torch, s.right), s.D, pv).cpu().numpy()
+    assert np.array_equal(want, st.match_host(Lp, Rp, s.D, pv, out=op))
 
 
 def test_repeat_runs_bit_identical(env):
