@@ -31,6 +31,8 @@
  *     the image); L_min and the regions use the opened arms.
  *   - support region (Eq. 2): union over q on the vertical arm of p of q's
  *     horizontal segment; N = its pixel count.  Reference-view arms only.
+ *     The other order (union over q on p's horizontal arm of q's vertical
+ *     segment) is available as a variant.
  *   - d in [0, D-1]; a match outside the image costs 1 (upper bound of Eq. 1).
  *   - WTA (Eq. 3) takes the smallest d among equal minima.
  *   - outlier removal: left-right consistency, valid iff x - dL >= 0 and
@@ -207,6 +209,7 @@ typedef struct {
     const uint8_t *ref_arms;
     int sign;                           /* -1: left reference (q = p - d); +1: right */
     orc_cost_params cp;
+    int order;                          /* 0: region H then V (Eq. 2 reading); 1: V then H */
 } view_ctx;
 
 static int lmin_of(const uint8_t *a)
@@ -230,14 +233,23 @@ static double pixel_cost(const view_ctx *v, int x, int y, int d)
                           v->cp.gamma_l, v->cp.eps);
 }
 
-/* Eq. 2 support-region size N of pixel (x, y) */
+/* Eq. 2 support-region size N of pixel (x, y): order 0 sums, over q on p's
+   vertical arm, q's horizontal segment; order 1 sums, over q on p's
+   horizontal arm, q's vertical segment */
 static long region_size(const view_ctx *v, int x, int y)
 {
     const uint8_t *ap = v->ref_arms + 4 * ((long)y * v->W + x);
     long n = 0;
-    for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {
-        const uint8_t *aq = v->ref_arms + 4 * ((long)yy * v->W + x);
-        n += (long)aq[0] + aq[1] + 1;
+    if (v->order == 0) {
+        for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {
+            const uint8_t *aq = v->ref_arms + 4 * ((long)yy * v->W + x);
+            n += (long)aq[0] + aq[1] + 1;
+        }
+    } else {
+        for (int xx = x - ap[0]; xx <= x + ap[1]; xx++) {
+            const uint8_t *aq = v->ref_arms + 4 * ((long)y * v->W + xx);
+            n += (long)aq[2] + aq[3] + 1;
+        }
     }
     return n;
 }
@@ -269,13 +281,27 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
 #pragma omp parallel for schedule(static)
         for (int y = ya; y < yb; y++)
             for (int x = 0; x < W; x++) C[(long)(y - ya) * W + x] = pixel_cost(v, x, y, d);
+        if (v->order == 0) {
+            /* segment sums along each row (q's horizontal segment) */
 #pragma omp parallel for schedule(static)
-        for (int y = ya; y < yb; y++) {
-            for (int x = 0; x < W; x++) {
-                const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
-                double s = 0.0;
-                for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += C[(long)(y - ya) * W + xx];
-                SH[(long)(y - ya) * W + x] = s;
+            for (int y = ya; y < yb; y++) {
+                for (int x = 0; x < W; x++) {
+                    const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
+                    double s = 0.0;
+                    for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += C[(long)(y - ya) * W + xx];
+                    SH[(long)(y - ya) * W + x] = s;
+                }
+            }
+        } else {
+            /* segment sums along each column (q's vertical segment), output rows only */
+#pragma omp parallel for schedule(static)
+            for (int y = y0; y < y1; y++) {
+                for (int x = 0; x < W; x++) {
+                    const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
+                    double s = 0.0;
+                    for (int yy = y - a[2]; yy <= y + a[3]; yy++) s += C[(long)(yy - ya) * W + x];
+                    SH[(long)(y - ya) * W + x] = s;
+                }
             }
         }
 #pragma omp parallel for schedule(static)
@@ -283,7 +309,10 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
             for (int x = 0; x < W; x++) {
                 const uint8_t *a = v->ref_arms + 4 * ((long)y * W + x);
                 double s = 0.0;
-                for (int yy = y - a[2]; yy <= y + a[3]; yy++) s += SH[(long)(yy - ya) * W + x];
+                if (v->order == 0)
+                    for (int yy = y - a[2]; yy <= y + a[3]; yy++) s += SH[(long)(yy - ya) * W + x];
+                else
+                    for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += SH[(long)(y - ya) * W + xx];
                 long i = (long)(y - y0) * W + x;
                 double cbar = s / (double)N[i];
                 if (vol) vol[(long)d * W * no + i] = cbar;
@@ -324,7 +353,7 @@ int orc_lr_check(const int16_t *dl, const int16_t *dr, int W, int rows, int tol,
  */
 int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
               double lambda_ad, double lambda_census, double gamma_l, double eps,
-              int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol, int smooth,
+              int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol, int smooth, int order,
               int y0, int y1,
               int16_t *disp_l, int16_t *disp_r, int16_t *disp_final,
               double *best_l, double *second_l, double *best_r, double *second_r,
@@ -348,8 +377,8 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
     }
     {
         orc_cost_params cp = {lambda_ad, lambda_census, gamma_l, eps};
-        view_ctx vl = {W, H, D, left, right, cl, cr, al, -1, cp};
-        view_ctx vr = {W, H, D, right, left, cr, cl, ar, +1, cp};
+        view_ctx vl = {W, H, D, left, right, cl, cr, al, -1, cp, order};
+        view_ctx vr = {W, H, D, right, left, cr, cl, ar, +1, cp, order};
         if ((rc = run_view(&vl, y0, y1, L1, disp_l, best_l, second_l, vol_l)) != ORC_OK) goto done;
         if ((rc = run_view(&vr, y0, y1, L1, disp_r, best_r, second_r, vol_r)) != ORC_OK) goto done;
         rc = orc_lr_check(disp_l, disp_r, W, y1 - y0, lr_tol, disp_final);

@@ -41,7 +41,7 @@ def lib():
         L.orc_cost_terms.argtypes = [i, i, i, d, d, d, d]
         L.orc_cost_terms.restype = d
         L.orc_lr_check.argtypes = [P, P, i, i, i, P]
-        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i] + [P] * 9
+        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i, i] + [P] * 9
         L.orc_arms_smooth.argtypes = [P, i, i, P]
         L.orc_arms_smooth.restype = i
         L.orc_vote.argtypes = [P, P, i, i, i, i, P]
@@ -75,6 +75,7 @@ class Params:
     tau2: int = 6
     lr_tol: int = 1               # reading; < 0 disables the check
     smooth_arms: int = 0          # reading of Sect. 4.1's morphological processing; 1 = 3x3 opening
+    agg_order: int = 0            # 0: region H then V (Eq. 2 reading); 1: V then H (variant)
 
 
 def _ptr(a: np.ndarray):
@@ -214,7 +215,7 @@ def match(left: np.ndarray, right: np.ndarray, D: int, p: Params = Params(),
     null = ctypes.c_void_p(0)
     _check(lib().orc_match(_ptr(left), _ptr(right), W, H, D, p.lambda_ad, p.lambda_census,
                            p.gamma_l, p.eps, p.census_w, p.census_h, p.arm_l1, p.arm_l2,
-                           p.tau1, p.tau2, p.lr_tol, p.smooth_arms, y0, y1,
+                           p.tau1, p.tau2, p.lr_tol, p.smooth_arms, p.agg_order, y0, y1,
                            _ptr(dl), _ptr(dr), _ptr(df), _ptr(bl), _ptr(sl), _ptr(br), _ptr(sr),
                            _ptr(vl) if volume else null, _ptr(vr) if volume else null))
     return MatchResult(dl, dr, df, bl, sl, br, sr, vl, vr, y0)

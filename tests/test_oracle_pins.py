@@ -679,3 +679,49 @@ def test_densify_minimises_the_energy_of_eq20():
         # zero directional derivative (central difference of a quadratic is exact)
         g = (DN.energy(D + 1e-3 * v, ds, B, mf, mi, dp) - DN.energy(D - 1e-3 * v, ds, B, mf, mi, dp)) / 2e-3
         assert abs(g) < 1e-7 * max(1.0, e0)
+
+
+# ----------------------------------------------------------------- aggregation order variant
+def _region_vh(arms_img, x, y):
+    """The other order as a coordinate set: for every q on p's horizontal arm,
+    the pixels of q's own vertical segment."""
+    l, r = int(arms_img[y, x, 0]), int(arms_img[y, x, 1])
+    pts = set()
+    for xx in range(x - l, x + r + 1):
+        qu, qd = int(arms_img[y, xx, 2]), int(arms_img[y, xx, 3])
+        for yy in range(y - qu, y + qd + 1):
+            pts.add((xx, yy))
+    return pts
+
+
+def test_v_then_h_aggregation_equals_brute_force_region_mean():
+    rng = np.random.default_rng(61)
+    base = rng.integers(0, 256, (3, 4, 3))
+    left = np.clip(np.kron(base, np.ones((4, 4, 1))) + rng.integers(-8, 9, (12, 16, 3)), 0, 255).astype(np.uint8)
+    right = np.roll(left, -2, axis=1)
+    right[:, -2:] = rng.integers(0, 256, (12, 2, 3))
+    p = O.Params(arm_l1=5, arm_l2=2, agg_order=1)
+    res = O.match(left, right, 5, p, volume=True)
+    C, al = _raw_costs_left(left, right, 5, p)
+    differs = False
+    for y in range(12):
+        for x in range(16):
+            pts = _region_vh(al, x, y)
+            differs |= pts != _region(al, x, y)
+            for d in range(5):
+                ref = sum(C[d, yy, xx] for xx, yy in pts) / len(pts)
+                assert res.vol_l[d, y, x] == pytest.approx(ref, rel=1e-12, abs=1e-15)
+    assert differs   # the two orders give different regions on this input
+
+
+def test_aggregation_orders_agree_on_box_arms():
+    # no colour stop and L2 = L1: every arm is the clipped box radius, so both
+    # orders cover the same clipped box
+    rng = np.random.default_rng(62)
+    left = rng.integers(0, 256, (14, 19, 3), dtype=np.uint8)
+    right = rng.integers(0, 256, (14, 19, 3), dtype=np.uint8)
+    kw = dict(arm_l1=3, arm_l2=3, tau1=256, tau2=256)
+    a = O.match(left, right, 4, O.Params(**kw), volume=True)
+    b = O.match(left, right, 4, O.Params(agg_order=1, **kw), volume=True)
+    assert np.allclose(a.vol_l, b.vol_l, rtol=1e-12, atol=1e-15)
+    assert np.array_equal(a.disp_l, b.disp_l) and np.array_equal(a.disp, b.disp)
