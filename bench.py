@@ -285,6 +285,7 @@ def own_arm(args):
         extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
         extras["smooth_config2"] = smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        extras["vh_order_config2"] = vh_order_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
         extras["densify_1280x720"] = densify_full_size(torch, binding, st, flush, dev)
         extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
         extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
@@ -419,6 +420,42 @@ def smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 
     return {"ms_path": round(t0, 4), "ms_path_smoothed": round(t1, 4),
             "k_smooth": {"launches_per_frame": n / reps, "avg_us": round(avg, 3) if avg else None,
                          "frac_hbm": round(alg / (avg * 1e-6) / 1e9 / pk["hbm_gbs"], 4) if avg else None}}
+
+
+# ----------------- the other aggregation order, Sect. 4.2.2 (config 2)
+def vh_order_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int = 20):
+    """The config 2 path with vertical sums first (k_vcost, then the row scan
+    k_hwta) against the default order; per-kernel CUDA-event averages."""
+    W, H = L.shape[1], L.shape[0]
+    out = torch.empty((H, W), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, order in (("hv", 0), ("vh", 1)):
+        p = binding.Params.default(d_chunk=dchunk, agg_order=order)
+        for _ in range(3):
+            st.match(L, R, D, p, out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.match(L, R, D, p, out)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        st.set_profiling(True)
+        st.profile_reset()
+        for _ in range(reps):
+            flush.zero_()
+            st.match(L, R, D, p, out)
+        torch.cuda.synchronize(dev)
+        prof = st.profile()
+        st.set_profiling(False)
+        res[f"ms_path_{name}"] = round(statistics.median(ts), 4)
+        for k in (("k_hagg", "k_vagg") if order == 0 else ("k_vcost", "k_hwta")):
+            n, ms = prof.get(k, (0, 0.0))
+            res[f"{k}_us"] = round(ms / n * 1e3, 3) if n else None
+    return res
 
 
 # --------------------------------------------- densification (Sect. 6)

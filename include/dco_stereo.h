@@ -74,7 +74,15 @@ typedef enum {
  *   smooth_arms = 0: with 1, the "morphological processing" of Sect. 4.1 is
  *   read as a grey-level opening (3x3 minimum, then 3x3 maximum, windows cut
  *   to the image) of each arm map; L_min, alpha and the support regions then
- *   follow the opened arms (dco_stereo_arms returns them too).
+ *   follow the opened arms (dco_stereo_arms returns them too);
+ *   agg_order = 0: the order of the two 1-D sums of the cross-region
+ *   aggregation (Sect. 4.2.2, Eq. 2).  0: horizontal sums along each pixel's
+ *   horizontal arm, then their sum over p's vertical arm (region = union
+ *   over q on p's vertical arm of q's horizontal segment).  1: vertical sums
+ *   first, then their sum over p's horizontal arm (region = union over q on
+ *   p's horizontal arm of q's vertical segment).  In both, N(p) of Eq. 2 is
+ *   the size of the region actually summed.  The Eq. 4 vote always counts
+ *   over the order-0 region.
  */
 typedef struct {
     float lambda_ad;
@@ -91,6 +99,7 @@ typedef struct {
     int d_chunk; /* disparities aggregated per pass (0 = automatic); see dco_stereo_match */
     int vote_iters; /* Eq. 4 rounds after the consistency check (0 = none) */
     int smooth_arms; /* 1: smooth cross-support window (Sect. 4.1), see above; 0 = raw arms */
+    int agg_order; /* 0: horizontal then vertical sums (Eq. 2); 1: vertical then horizontal */
 } dco_params;
 
 /* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */

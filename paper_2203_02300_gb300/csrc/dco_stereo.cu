@@ -455,6 +455,105 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
               (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32 + lane, a.dstride);
 }
 
+// ---------------------------------------------------------------- k_vcost
+// The other aggregation order, first pass: Eq. 1 costs and their vertical
+// segment sums S_V(q, d) over q's vertical arm.  Block = one column x (a
+// chunk of rows) of one reference view for one group of 32 disparities;
+// lane = disparity.  The reference records of the column are staged in
+// shared memory; the candidates of each row (32 neighbouring records of the
+// other view's row) are read straight from the record rows.  Then the phases
+// of k_hagg along the column: warp segments of 32 rows, offsets, segment
+// sums (hagg_tail, with the up / down arms), written to the same slice layout.
+struct CSmem {
+    int ref, arm, p, t, total;
+    __host__ __device__ CSmem(int len, int chunk, int nw)
+    {
+        ref = kTabBytes;
+        arm = ref + len * 16;
+        p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
+        t = p + len * 128;
+        total = t + nw * 128;
+    }
+};
+
+__device__ __forceinline__ void vcost_body(const HArgs &a, int bx, int by, int bz)
+{
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int W = a.W, H = a.H, L1 = a.L1;
+    const int x = bx;
+    const int view = bz / a.ngroups, g = bz % a.ngroups;
+    const int ys = by * a.chunk, ye = min(H, ys + a.chunk);
+    const int ya = max(0, ys - L1), yb = min(H, ye + L1), len = yb - ya;
+    const CSmem L(len, a.chunk, nw);
+    const float *sTA = reinterpret_cast<const float *>(smem_raw);
+    const float *sTC = sTA + kTabAD;
+    uint4 *sref = reinterpret_cast<uint4 *>(smem_raw + L.ref);
+    uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);   // (up, down) of the output rows
+    uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);    // [len][32], P[-1] = 0
+    uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);
+    const uint4 *rref = view ? a.rec[1] : a.rec[0];   // padded rows, pitch rpitch
+    const uint4 *roth = view ? a.rec[0] : a.rec[1];
+    const uchar4 *aref = view ? a.arms[1] : a.arms[0];
+
+    for (int i = threadIdx.x; i < kTabBytes / 16; i += blockDim.x)
+        cp_async16(smem_raw + 16 * i, reinterpret_cast<const uint8_t *>(a.tables) + 16 * i);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) cp_async16(sref + i, rref + (size_t)(ya + i) * a.rpitch + x);
+    for (int i = threadIdx.x; i < ye - ys; i += blockDim.x) {
+        const uchar4 am = aref[(size_t)(ys + i) * W + x];
+        sarm[i] = make_uchar4(am.z, am.w, 0, 0);   // backward = up, forward = down
+    }
+    if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int dlo = a.d0 + 32 * g;
+    const int dhi = min(min(a.d0 + a.dc, a.D), dlo + 32) - 1;
+    const int d = dlo + lane;
+    const int dd = d <= dhi ? d : dlo;                // dead lanes read a real candidate, results unused
+    const int xo = view ? x + dd : x - dd;            // candidate column, -255 .. W + 254 (padded rows)
+    const bool outside = xo < 0 || xo >= W;           // match outside the image: cost 1
+    const uint4 *cand = roth + xo;
+    const float Sf = a.S;
+    const uint32_t Sint = a.Sint;
+
+    // ---- A: costs down this warp's segment of rows, local prefix
+    const int sa = warp * kHSegCost, sb = min(len, sa + kHSegCost);   // rows relative to ya
+    uint32_t run = 0;
+    int u = sa;
+    for (; u + 4 <= sb; u += 4) {
+        uint4 po[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) po[k] = __ldg(cand + (size_t)(ya + u + k) * a.rpitch);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint4 pr = sref[u + k];
+            const int hm = __popc(pr.x ^ po[k].x) + __popc(pr.y ^ po[k].y);
+            const int kk = (int)__dp4a(__vabsdiffu4(pr.z, po[k].z), 0x00010101u, 0u);
+            const float av = __uint_as_float(pr.w);
+            const uint32_t q = __float2uint_rn(fmaf(av, sTA[kk], (Sf - av) * sTC[hm]));
+            run += outside ? Sint : q;
+            P[(u + k) * 32 + lane] = run;
+        }
+    }
+    for (; u < sb; u++) {
+        const uint4 po = __ldg(cand + (size_t)(ya + u) * a.rpitch);
+        const uint4 pr = sref[u];
+        const int hm = __popc(pr.x ^ po.x) + __popc(pr.y ^ po.y);
+        const int kk = (int)__dp4a(__vabsdiffu4(pr.z, po.z), 0x00010101u, 0u);
+        const float av = __uint_as_float(pr.w);
+        const uint32_t q = __float2uint_rn(fmaf(av, sTA[kk], (Sf - av) * sTC[hm]));
+        run += outside ? Sint : q;
+        P[u * 32 + lane] = run;
+    }
+    T[warp * 32 + lane] = run;
+    __syncthreads();
+    // consecutive output rows are one slice row (W * dstride words) apart
+    hagg_tail(P, T, sarm, sa, sb, ye - ys, ys - ya,
+              (view ? a.sh[1] : a.sh[0]) + ((size_t)ys * W + x) * a.dstride + g * 32 + lane,
+              (size_t)W * a.dstride);
+}
+
 // ---------------------------------------------------------------- k_hvote
 // Horizontal pass of the parallax optimisation (Sect. 4.3, Eq. 4): the same
 // block layout and phases as k_hagg, with the cost replaced by the indicator
@@ -530,25 +629,34 @@ __host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (siz
 // kMax: the WTA takes the largest V (the vote counts of Eq. 4) instead of the
 // smallest: V is complemented, so the strict < keeps the smallest d on ties
 // and the key merge across passes is unchanged
-template <bool kMax>
+//
+// kRow: the other aggregation order (the region is the union over q on p's
+// horizontal arm of q's vertical segment): the block is one row y, the scan
+// runs along x over the vertical segment sums, the window is p's horizontal
+// arm and the region size adds u + d + 1 of every column.  Below, "rows" are
+// the scan positions.
+template <bool kMax, bool kRow>
 __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint32_t vsmem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int W = a.W, H = a.H, L1 = a.L1;
-    const int x = bx, view = by;
-    const int ys = bz * a.chunk, ye = min(H, ys + a.chunk);
-    const int ya = max(0, ys - L1), yb = min(H, ye + L1);
+    const int fix = bx, view = by;              // the column x (kRow: the row y)
+    const int E = kRow ? W : H;                 // extent of the scan
+    const int ys = bz * a.chunk, ye = min(E, ys + a.chunk);
+    const int ya = max(0, ys - L1), yb = min(E, ye + L1);
     const int len = yb - ya;
+    auto pix = [&](int sp) -> size_t { return kRow ? (size_t)fix * W + sp : (size_t)sp * W + fix; };
     uint32_t *Q = vsmem + kQS;                // [len][kQS], Q[-1] = 0
     uint32_t *T = Q + len * kQS;              // [nw][32] segment sums
     uint32_t *NQ = T + nw * 32;               // [len] prefix of l + r + 1
     uint32_t *NT = NQ + len;                  // [nw]
     uint32_t *AW = NT + nw;                   // [len] arm words
 
-    const uint32_t *sh = (view ? a.sh[1] : a.sh[0]) + (size_t)x * a.dstride + lane;
-    const uint32_t *arms = reinterpret_cast<const uint32_t *>(view ? a.arms[1] : a.arms[0]) + x;
-    const size_t rowstride = (size_t)W * a.dstride;
+    const uint32_t *sh = (view ? a.sh[1] : a.sh[0]) + pix(0) * a.dstride + lane;
+    const uint32_t *arms = reinterpret_cast<const uint32_t *>(view ? a.arms[1] : a.arms[0]) + pix(0);
+    const size_t rowstride = kRow ? (size_t)a.dstride : (size_t)W * a.dstride;   // between scan positions
+    const size_t astride = kRow ? 1 : (size_t)W;
     const int sa = warp * kVSeg, sb = min(len, sa + kVSeg);   // relative to ya
     const bool full = sb - sa == kVSeg;
     const int ng = (a.dc + 31) / 32;
@@ -574,9 +682,13 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     // arm word of this lane's row and the region-size prefix (d independent)
     const int r = sa + lane;
     const bool rin = r < sb;
-    const uint32_t aw = rin ? __ldg(arms + (size_t)(ya + r) * W) : 0u;
+    const uint32_t aw = rin ? __ldg(arms + (size_t)(ya + r) * astride) : 0u;
+    // window arms along the scan (computed where used: short live ranges),
+    // and the segment length across it
+    auto back = [&]() { return kRow ? (int)(aw & 0xffu) : (int)((aw >> 16) & 0xffu); };
+    auto fwd = [&]() { return kRow ? (int)((aw >> 8) & 0xffu) : (int)(aw >> 24); };
     {
-        uint32_t nv = rin ? (aw & 0xffu) + ((aw >> 8) & 0xffu) + 1u : 0u;
+        uint32_t nv = !rin ? 0u : kRow ? ((aw >> 16) & 0xffu) + (aw >> 24) + 1u : (aw & 0xffu) + ((aw >> 8) & 0xffu) + 1u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {   // inclusive scan across the segment's rows
             const uint32_t t = __shfl_up_sync(0xffffffffu, nv, o);
@@ -624,9 +736,8 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         const int dbase = a.d0 + g * 32;
         const int nlive = max(0, min(32, min(a.dc - g * 32, a.D - dbase)));
         if (out_row) {
-            const int up = (aw >> 16) & 0xff, dn = aw >> 24;
-            const uint32_t *qh = Q + (r + dn) * kQS;
-            const int lo = r - up - 1;               // >= -1
+            const uint32_t *qh = Q + (r + fwd()) * kQS;
+            const int lo = r - back() - 1;           // >= -1
             const uint32_t *ql = Q + lo * kQS;
             // running minimum; strict < keeps the smallest d on ties
             uint32_t bj = 0xffffffffu, bmin = bv;
@@ -646,10 +757,10 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             }
             if (bj != 0xffffffffu) { bv = bmin; bd = (uint32_t)dbase + bj; }
             if (want_vol) {
-                const uint32_t n = NQ[r + dn] - (lo >= 0 ? NQ[lo] : 0u);
+                const uint32_t n = NQ[r + fwd()] - (lo >= 0 ? NQ[lo] : 0u);
                 for (int j = 0; j < nlive; j++) {
                     const uint32_t vv = qh[j] - ql[j];
-                    a.vol[((size_t)(dbase + j) * H + ya + r) * W + x] = float(vv) / (float(n) * a.S);
+                    a.vol[(size_t)(dbase + j) * H * W + pix(ya + r)] = float(vv) / (float(n) * a.S);
                 }
             }
         }
@@ -660,7 +771,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     unsigned long long *best = view ? a.best[1] : a.best[0];
     int16_t *disp = view ? a.disp[1] : a.disp[0];
     float *cost = view ? a.cost[1] : a.cost[0];
-    const size_t i = (size_t)(ya + r) * W + x;
+    const size_t i = pix(ya + r);
     unsigned long long key = ((unsigned long long)bv << 32) | bd;
     if (!a.first) {
         const unsigned long long prev = best[i];
@@ -670,9 +781,8 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         const bool invalid = kMax && (a.mask[i] < 0 || a.mask[i] >= a.D);   // Eq. 4: no vote, stays invalid
         disp[i] = invalid ? (int16_t)-1 : (int16_t)(key & 0xffffffffu);
         if (cost) {
-            const int up = (aw >> 16) & 0xff, dn = aw >> 24;
-            const int lo = r - up - 1;
-            const uint32_t n = NQ[r + dn] - (lo >= 0 ? NQ[lo] : 0u);
+            const int lo = r - back() - 1;
+            const uint32_t n = NQ[r + fwd()] - (lo >= 0 ? NQ[lo] : 0u);
             cost[i] = float(uint32_t(key >> 32)) / (float(n) * a.S);
         }
     } else {
@@ -794,12 +904,20 @@ __global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __g
     hagg_body(b.p[i], bx, by, bz);
 }
 
-template <int N, bool kMax>
+template <int N, bool kMax, bool kRow = false>
 __global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
 {
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
-    vagg_body<kMax>(b.p[i], bx, by, bz);
+    vagg_body<kMax, kRow>(b.p[i], bx, by, bz);
+}
+
+template <int N>
+__global__ void __launch_bounds__(1024) k_vcost(const __grid_constant__ Batch<HArgs, N> b)
+{
+    int bx, by, bz;
+    const int i = batch_pair(b, blockIdx.x, bx, by, bz);
+    vcost_body(b.p[i], bx, by, bz);
 }
 
 template <int N>
@@ -849,6 +967,7 @@ struct Derived {
     int L1;
     uint32_t Sint;
     float S;
+    int order;   // aggregation order: 0 horizontal then vertical, 1 vertical then horizontal
 };
 
 struct Layout {
@@ -869,6 +988,7 @@ bool derive(const dco_params &p, Derived &d)
     s = std::min(s, 1048576.0);
     d.Sint = (uint32_t)s;
     d.S = (float)s;
+    d.order = p.agg_order;
     return true;
 }
 
@@ -882,6 +1002,7 @@ bool params_valid(const dco_params &p)
     if (p.d_chunk < 0) return false;
     if (p.vote_iters < 0 || p.vote_iters > 64) return false;
     if (p.smooth_arms != 0 && p.smooth_arms != 1) return false;
+    if (p.agg_order != 0 && p.agg_order != 1) return false;
     return true;
 }
 
@@ -933,6 +1054,20 @@ struct HGeom {
     size_t smem;
     dim3 grid;
 };
+
+// the other aggregation order: k_vcost walks columns (one chunk of rows per
+// block while it fits 32 warps of 32 rows), k_vagg<.., kRow> rows (the scan
+// range along x at most 512 columns, like k_vagg's rows)
+HGeom vcost_geom(int W, int H, int dc, int L1)
+{
+    HGeom g{};
+    g.chunk = H <= kHMaxLen ? H : 512;
+    const int len = std::min(H, g.chunk + 2 * L1);
+    g.nw = (len + kHSegCost - 1) / kHSegCost;
+    g.smem = CSmem(len, g.chunk, g.nw).total;
+    g.grid = dim3(W, (H + g.chunk - 1) / g.chunk, 2 * ((dc + 31) / 32));
+    return g;
+}
 
 HGeom hagg_geom(int W, int H, int dc, int L1)
 {
@@ -1314,14 +1449,14 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
     std::map<int, std::vector<Item<HArgs>>> hb;
     std::map<int, std::vector<Item<VArgs>>> vb;
     std::map<int, size_t> hsm, vsm;
+    const bool vh = dv.order == 1;   // vertical segment sums first (k_vcost), then rows (k_vagg<.., kRow>)
     for (const Job &j : jobs) {
         if (pass >= j.L.npass) continue;
         const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
-        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
-        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
-        const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
-        hsm[hg.nw] = std::max(hsm[hg.nw], (size_t)HSmem(hlen, hg.chunk, hg.nw).total);
-        vsm[vg.nw] = std::max(vsm[vg.nw], vagg_smem_words(vlen, vg.nw) * 4);
+        const HGeom hg = vh ? vcost_geom(j.W, j.H, dc, dv.L1) : hagg_geom(j.W, j.H, dc, dv.L1);
+        const VGeom vg = vh ? vagg_geom(j.H, j.W, dv.L1) : vagg_geom(j.W, j.H, dv.L1);
+        hsm[hg.nw] = std::max(hsm[hg.nw], hg.smem);
+        vsm[vg.nw] = std::max(vsm[vg.nw], vg.smem);
         Item<HArgs> a{};
         for (int v = 0; v < 2; v++) {
             a.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
@@ -1351,6 +1486,12 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         vb[vg.nw].push_back(b);
     }
     for (auto &kv : hb) {
+        if (vh) {
+            dco_status st = launch_items(h, s, "k_vcost", k_vcost<1>, k_vcost<kBatchMax>, kv.second, kv.first * 32,
+                                         hsm[kv.first]);
+            if (st != DCO_OK) return st;
+            continue;
+        }
         dco_status st = kv.first <= kHNarrow
                             ? launch_items(h, s, "k_hagg", k_hagg<1, false>, k_hagg<kBatchMax, false>, kv.second,
                                            kv.first * 32, hsm[kv.first])
@@ -1359,8 +1500,10 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         if (st != DCO_OK) return st;
     }
     for (auto &kv : vb) {
-        dco_status st = launch_items(h, s, "k_vagg", k_vagg<1, false>, k_vagg<kBatchMax, false>, kv.second, kv.first * 32,
-                                     vsm[kv.first]);
+        dco_status st = vh ? launch_items(h, s, "k_hwta", k_vagg<1, false, true>, k_vagg<kBatchMax, false, true>,
+                                          kv.second, kv.first * 32, vsm[kv.first])
+                           : launch_items(h, s, "k_vagg", k_vagg<1, false>, k_vagg<kBatchMax, false>, kv.second,
+                                          kv.first * 32, vsm[kv.first]);
         if (st != DCO_OK) return st;
     }
     return DCO_OK;
@@ -1539,6 +1682,7 @@ dco_status dco_params_default(dco_params *p)
     p->d_chunk = 0;
     p->vote_iters = 0;
     p->smooth_arms = 0;
+    p->agg_order = 0;
     return DCO_OK;
 }
 

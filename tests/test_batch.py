@@ -158,3 +158,16 @@ def test_batch_with_smoothing_equals_single(env, config3):
     torch.cuda.synchronize()
     for s, (_, _, _, out) in zip(sub, pairs):
         assert np.array_equal(out.cpu().numpy(), _single(env, s, p))
+
+
+def test_batch_vh_order_equals_single(env, config3):
+    # the other aggregation order: batched k_vcost / k_vagg row launches
+    torch, binding, st = env
+    p = binding.Params.default(agg_order=1)
+    sub = config3[:8]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")) for s in sub]
+    st.match_batch(pairs, p)
+    torch.cuda.synchronize()
+    for s, (_, _, _, out) in zip(sub, pairs):
+        assert np.array_equal(out.cpu().numpy(), _single(env, s, p))

@@ -35,7 +35,8 @@ def oparams(bp):
     return O.Params(lambda_ad=float(bp.lambda_ad), lambda_census=float(bp.lambda_census),
                     gamma_l=float(bp.gamma_l), eps=float(bp.eps), census_w=bp.census_w,
                     census_h=bp.census_h, arm_l1=bp.arm_l1, arm_l2=bp.arm_l2, tau1=bp.tau1,
-                    tau2=bp.tau2, lr_tol=bp.lr_tol, smooth_arms=bp.smooth_arms)
+                    tau2=bp.tau2, lr_tol=bp.lr_tol, smooth_arms=bp.smooth_arms,
+                    agg_order=bp.agg_order)
 
 
 def run_views(env, left, right, D, bp=None):
@@ -178,6 +179,75 @@ def test_parameter_variants(env, over):
     torch, binding, st = env
     s = scenes.config_scene(1)
     full_check(env, s.left, s.right, s.D, binding.Params.default(**over))
+
+
+# ------------------------------------------- the other aggregation order
+# region = union over q on p's horizontal arm of q's vertical segment
+# (k_vcost column sums, then k_vagg scanning rows)
+def test_vh_order_config1_full_parity(env):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    n, out, dl, dr = full_check(env, s.left, s.right, s.D, binding.Params.default(agg_order=1))
+    gt = np.rint(s.disp).astype(np.int16)
+    assert ((dl == gt) & ~s.occluded).sum() / (~s.occluded).sum() > 0.99
+
+
+def test_vh_order_differs_from_hv_order(env):
+    # the two regions differ wherever arms of neighbours differ: the costs
+    # must not be equal everywhere (guards against a silent order-0 run)
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    a = run_views(env, s.left, s.right, s.D)
+    b = run_views(env, s.left, s.right, s.D, binding.Params.default(agg_order=1))
+    assert not np.array_equal(a[3], b[3])
+
+
+# (D <= W is a library rule); 20x1100: columns longer than one k_vcost chunk
+@pytest.mark.parametrize("W,H,D", [(1, 1, 1), (7, 5, 3), (33, 17, 16), (3, 100, 3), (100, 3, 40),
+                                   (40, 65, 33), (97, 71, 50), (600, 20, 64), (20, 1100, 16)])
+def test_vh_order_ragged_sizes(env, W, H, D):
+    torch, binding, st = env
+    s = scenes.plane_scene(W, H, D, 3, seed=2000 + W * H + D, drange=(0, max(0, min(D - 1, W - 1))),
+                           noise_sigma=1.0) if W >= 8 and H >= 8 else None
+    if s is None:
+        left, right = scenes.random_pair(W, H, 11 * W + H)
+    else:
+        left, right = s.left, s.right
+    full_check(env, left, right, D, binding.Params.default(agg_order=1))
+
+
+@pytest.mark.parametrize("over", [dict(d_chunk=5), dict(d_chunk=33), dict(smooth_arms=1),
+                                  dict(arm_l1=5, arm_l2=2), dict(arm_l1=40, arm_l2=40, tau1=256, tau2=256)])
+def test_vh_order_variants(env, over):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    full_check(env, s.left, s.right, s.D, binding.Params.default(agg_order=1, **over))
+
+
+def test_vh_order_cost_volume(env):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    ref = O.match(s.left, s.right, s.D, O.Params(agg_order=1), volume=True)
+    L, R = dev(torch, s.left), dev(torch, s.right)
+    got = st.cost_volume(L, R, s.D, 0, binding.Params.default(agg_order=1)).cpu().numpy()
+    parity.check_volume(got, ref.vol_l, "volume view 0, order 1")
+
+
+def test_vh_order_config5_sampled_rows(env):
+    # 1920x1080 D=256: k_vcost sums the 1080-row columns in chunks of 512
+    # rows (rows 509..515 straddle the first boundary), k_vagg scans the
+    # 1920-column rows in several chunks
+    torch, binding, st = env
+    s = scenes.config_scene(5)
+    bp = binding.Params.default(agg_order=1)
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D, bp)
+    for rows in ((0, 6), (509, 515), (1074, 1080)):
+        ref = O.match(s.left, s.right, s.D, O.Params(agg_order=1), rows=rows)
+        sl = slice(*rows)
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r)
+        parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
+        parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
 
 
 def test_config5_sampled_rows(env):
