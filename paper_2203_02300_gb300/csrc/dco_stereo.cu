@@ -610,21 +610,78 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
 // Block = one column x of one reference view, a chunk of output rows.  The
 // prefix range [ya, yb) is split into warp segments of 32 rows.  For each
 // group of 32 disparities of the pass:
-//   A. lane = disparity: each warp loads its 32 slice rows into registers
-//      (one 128-byte line per row), sums them, exchanges the segment sums
-//      with the other warps, and writes the column prefix (with its segment
-//      offset) to Q[y - ya][lane] (row stride 33 words): one shared store per
-//      evaluation;
+//   0. every warp moves its 32 slice rows (128 bytes each: the group's
+//      disparities of one pixel) into Q[y - ya] with one TMA tile copy
+//      (completing on the warp's mbarrier);
+//   A. lane = disparity: the segment sum, exchanged with the other warps,
+//      then the column prefix (with its segment offset) written back in
+//      place;
 //   C. lane = output row: V(d) = Q(y + dn, d) - Q(y - up - 1, d) for the 32
 //      disparities (Eq. 2: the sum over the vertical arm of the horizontal
 //      sums; N does not depend on d, so the WTA compares V), running minimum
-//      with the smallest d on ties (Eq. 3) in registers across groups.
+//      with the smallest d on ties (Eq. 3) in registers across groups; four
+//      disparities per 16-byte shared load.
 // Finally the running best is merged with earlier passes and written.
-constexpr int kQS = 33;   // Q row stride: column d of consecutive rows hits distinct banks
+// Q rows are 36 words (144 bytes: the tile box is 32 disparities plus 4
+// zero-filled words, a multiple of 16 bytes); in phase C the 16-byte loads
+// of 32 rows spread over the 8 bank quads.
+constexpr int kQS = 36;   // Q row stride in words
 constexpr int kVSeg = 32; // rows per warp
+constexpr int kQ0 = 64;   // Q[0] at word 64 (256 bytes): every warp's tile starts on a 128-byte boundary
+constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a copy is declared lost
+constexpr int kStatusCopyTimeout = 1; // status word: a tile copy did not complete
+constexpr int kStatusAlign = 2;       // status word: shared memory not aligned for the tile copies
+constexpr uint32_t kVTileBytes = kVSeg * kQS * 4;
 
-// Q has one extra row of zeros in front (Q[-1], the prefix before the first row)
-__host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return (size_t)(len + 1) * kQS + nw * 32 + 2 * len + nw; }
+// words before the mbarriers: Q[-1] (zeros, at kQ0 - kQS) and Q [nw*32 rows:
+// every warp's tile is 32 rows], T [nw][32], NQ [len], NT [nw]
+__host__ __device__ inline size_t vagg_bar_word(int len, int nw)
+{
+    return ((size_t)kQ0 + (size_t)nw * kVSeg * kQS + nw * 32 + len + nw + 1) / 2 * 2;
+}
+__host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return vagg_bar_word(len, nw) + 2 * nw; }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitLimit; i++) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+                 : "memory");
+}
+// TMA tile copy of the box at coordinates (c0, c1, c2, c3) of map `tm` to
+// shared address `dst` (128-byte aligned), completing on mbarrier `bar`
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+                 : "memory");
+}
 
 // kMax: the WTA takes the largest V (the vote counts of Eq. 4) instead of the
 // smallest: V is complemented, so the strict < keeps the smallest d on ties
@@ -647,37 +704,42 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     const int ya = max(0, ys - L1), yb = min(E, ye + L1);
     const int len = yb - ya;
     auto pix = [&](int sp) -> size_t { return kRow ? (size_t)fix * W + sp : (size_t)sp * W + fix; };
-    uint32_t *Q = vsmem + kQS;                // [len][kQS], Q[-1] = 0
-    uint32_t *T = Q + len * kQS;              // [nw][32] segment sums
+    uint32_t *Q = vsmem + kQ0;                // [nw * 32][kQS], Q[-1] = 0
+    uint32_t *T = Q + nw * kVSeg * kQS;       // [nw][32] segment sums
     uint32_t *NQ = T + nw * 32;               // [len] prefix of l + r + 1
     uint32_t *NT = NQ + len;                  // [nw]
-    uint32_t *AW = NT + nw;                   // [len] arm words
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(vsmem) + 4u * (uint32_t)vagg_bar_word(len, nw) + 8u * warp;
+    if (((uint32_t)__cvta_generic_to_shared(Q) & 127u) != 0) {   // the tile copies need 128-byte alignment
+        if (threadIdx.x == 0) atomicOr(a.status, kStatusAlign);
+        return;
+    }
 
-    const uint32_t *sh = (view ? a.sh[1] : a.sh[0]) + pix(0) * a.dstride + lane;
+    const CUtensorMap *tm = view ? &a.tm[1] : &a.tm[0];
     const uint32_t *arms = reinterpret_cast<const uint32_t *>(view ? a.arms[1] : a.arms[0]) + pix(0);
-    const size_t rowstride = kRow ? (size_t)a.dstride : (size_t)W * a.dstride;   // between scan positions
     const size_t astride = kRow ? 1 : (size_t)W;
     const int sa = warp * kVSeg, sb = min(len, sa + kVSeg);   // relative to ya
-    const bool full = sb - sa == kVSeg;
+    const int nrow = max(0, sb - sa);
     const int ng = (a.dc + 31) / 32;
     const bool want_vol = a.vol != nullptr && view == a.vol_view;
 
-    // one 64-bit base per group, 32-bit row offsets (31 * W * dstride < 2^32
-    // for W <= 16384, D <= 256); full segments need no predicates
-    uint32_t v[kVSeg];
-    auto load = [&](int g) {
-        const uint32_t *src = sh + (size_t)(ya + sa) * rowstride + g * 32;
-        const uint32_t rs = (uint32_t)rowstride;
-        uint32_t off = 0;
-        if (full) {
-#pragma unroll
-            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = __ldg(src + off);
-        } else {
-#pragma unroll
-            for (int u = 0; u < kVSeg; u++, off += rs) v[u] = sa + u < sb ? __ldg(src + off) : 0u;
-        }
+    if (lane == 0) mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    __syncwarp();
+    // group g's 32 rows of this warp's segment -> Q[sa .. sa + 31] (rows
+    // past the image are zero-filled, rows past yb are read and unused; the
+    // generic accesses of the previous group are ordered before the copy by
+    // the block barrier and the proxy fence)
+    auto issue = [&](int g) {
+        if (nrow == 0 || lane != 0) return;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(bar, kVTileBytes);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Q + sa * kQS);
+        if (a.tm_rank == 4)
+            tma_load_4d(dst, tm, 0, g, kRow ? ya + sa : fix, kRow ? fix : ya + sa, bar);
+        else
+            tma_load_3d(dst, tm, 32 * g, kRow ? ya + sa : fix, kRow ? fix : ya + sa, bar);
     };
-    load(0);   // the first group's rows are in flight during the arm-word work
+    issue(0);   // the first group's rows are in flight during the arm-word work
 
     // arm word of this lane's row and the region-size prefix (d independent)
     const int r = sa + lane;
@@ -694,19 +756,25 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             const uint32_t t = __shfl_up_sync(0xffffffffu, nv, o);
             if (lane >= o) nv += t;
         }
-        if (rin) { AW[r] = aw; NQ[r] = nv; }
+        if (rin) NQ[r] = nv;
         if (lane == 31) NT[warp] = nv;
     }
     const bool out_row = rin && ya + r >= ys && ya + r < ye;
     uint32_t bv = 0xffffffffu, bd = 0;
     if (warp == 0) Q[-kQS + lane] = 0u;   // Q[-1]: read by rows whose up arm reaches the top
+    bool lost = false;
 
     for (int g = 0; g < ng; g++) {
-        // ---- A: this warp's 32 rows of the slice column, lane = disparity
-        if (g > 0) load(g);
+        // ---- A: this warp's rows of the slice column, lane = disparity
+        if (nrow > 0 && !mbar_wait(bar, (uint32_t)(g & 1))) lost = true;
+        uint32_t *q = Q + sa * kQS + lane;
         uint32_t tot = 0;
-#pragma unroll
-        for (int u = 0; u < kVSeg; u++) tot += v[u];
+        if (nrow == kVSeg) {
+#pragma unroll 8
+            for (int u = 0; u < kVSeg; u++) tot += q[u * kQS];
+        } else {
+            for (int u = 0; u < nrow; u++) tot += q[u * kQS];
+        }
         T[warp * 32 + lane] = tot;
         __syncthreads();
         uint32_t run = 0;
@@ -717,18 +785,16 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             for (int w = 0; w < warp; w++) noff += NT[w];
             if (rin) NQ[r] += noff;
         }
-        uint32_t *q = Q + sa * kQS + lane;
-        if (full) {
-#pragma unroll
+        if (nrow == kVSeg) {
+#pragma unroll 8
             for (int u = 0; u < kVSeg; u++) {
-                run += v[u];
+                run += q[u * kQS];
                 q[u * kQS] = run;
             }
         } else {
-#pragma unroll
-            for (int u = 0; u < kVSeg; u++) {
-                run += v[u];
-                if (sa + u < sb) q[u * kQS] = run;
+            for (int u = 0; u < nrow; u++) {
+                run += q[u * kQS];
+                q[u * kQS] = run;
             }
         }
         __syncthreads();
@@ -742,11 +808,17 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             // running minimum; strict < keeps the smallest d on ties
             uint32_t bj = 0xffffffffu, bmin = bv;
             if (nlive == 32) {
-#pragma unroll 8
-                for (int j = 0; j < 32; j++) {
-                    const uint32_t vv = kMax ? ~(qh[j] - ql[j]) : qh[j] - ql[j];
-                    bj = vv < bmin ? (uint32_t)j : bj;
-                    bmin = min(bmin, vv);
+                const uint4 *qh4 = reinterpret_cast<const uint4 *>(qh), *ql4 = reinterpret_cast<const uint4 *>(ql);
+#pragma unroll 2
+                for (int j4 = 0; j4 < 8; j4++) {
+                    const uint4 h4 = qh4[j4], l4 = ql4[j4];
+                    const uint32_t hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const uint32_t vv = kMax ? ~(hv[k] - lv[k]) : hv[k] - lv[k];
+                        bj = vv < bmin ? (uint32_t)(4 * j4 + k) : bj;
+                        bmin = min(bmin, vv);
+                    }
                 }
             } else {
                 for (int j = 0; j < nlive; j++) {
@@ -765,6 +837,14 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             }
         }
         __syncthreads();   // Q and T are reused by the next group
+        if (g + 1 < ng) issue(g + 1);
+    }
+    if (lost) {
+        // a copy never completed: report, and give the others in flight a
+        // last bounded wait before the block's shared memory is released
+        if (lane == 0) atomicOr(a.status, kStatusCopyTimeout);
+        mbar_wait(bar, (uint32_t)((ng - 1) & 1));
+        return;
     }
     // ---- merge with earlier passes, write the disparity (last pass) or state
     if (!out_row) return;
@@ -905,7 +985,7 @@ __global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __g
 }
 
 template <int N, bool kMax, bool kRow = false>
-__global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
+__global__ void __launch_bounds__(16 * 32, 3) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
 {
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
@@ -1102,6 +1182,27 @@ VGeom vagg_geom(int W, int H, int L1)
     return g;
 }
 
+// ---- TMA tile maps of the slices (k_vagg)
+using TmapEncode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncode tmap_encoder()
+{
+    static TmapEncode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TmapEncode>(f);
+    });
+    return fn;
+}
+
+
 } // namespace
 
 struct dco_stereo {
@@ -1263,6 +1364,12 @@ T *ws_ptr(dco_stereo *h, size_t off) { return reinterpret_cast<T *>(h->ws + off)
 // image 0 go to arms0 (the caller's buffer for the arms entry point)
 // ----------------------------------------------------------- batched launches
 constexpr int kBatchMax = 64;   // pairs per launch (kernel parameter space)
+// pairs per launch of a kind of argument block: the V blocks carry two
+// tensor maps, so half as many fit the 32764 bytes of kernel parameters
+template <class A> constexpr int batch_max() { return sizeof(A) > 256 ? kBatchMax / 2 : kBatchMax; }
+static_assert(sizeof(Batch<VArgs, batch_max<VArgs>()>) <= 32764, "kernel parameters of a full V batch");
+static_assert(sizeof(Batch<HArgs, batch_max<HArgs>()>) <= 32764, "kernel parameters of a full H batch");
+constexpr int kVBatch = batch_max<VArgs>();
 
 // The dynamic shared-memory limit is an attribute of the kernel on a device,
 // shared by every handle and thread of the process: it is raised under a lock
@@ -1318,16 +1425,18 @@ dco_status launch_group(dco_stereo *h, cudaStream_t s, const char *name, K kerne
     return DCO_OK;
 }
 
-// one launch for a single pair (small parameter block), else groups of kBatchMax
+// one launch for a single pair (small parameter block), else groups of
+// batch_max<A>() (kn is the kernel instance for that many)
 template <class A, class K1, class KN>
 dco_status launch_items(dco_stereo *h, cudaStream_t s, const char *name, K1 k1, KN kn,
                         const std::vector<Item<A>> &items, int block, size_t smem)
 {
+    constexpr int nmax = batch_max<A>();
     if (items.empty()) return DCO_OK;
     if (items.size() == 1) return launch_group<A, 1>(h, s, name, k1, items.data(), 1, block, smem);
-    for (size_t i = 0; i < items.size(); i += kBatchMax) {
-        const int n = (int)std::min<size_t>(kBatchMax, items.size() - i);
-        dco_status st = launch_group<A, kBatchMax>(h, s, name, kn, items.data() + i, n, block, smem);
+    for (size_t i = 0; i < items.size(); i += nmax) {
+        const int n = (int)std::min<size_t>(nmax, items.size() - i);
+        dco_status st = launch_group<A, nmax>(h, s, name, kn, items.data() + i, n, block, smem);
         if (st != DCO_OK) return st;
     }
     return DCO_OK;
@@ -1444,6 +1553,49 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
 // pass `pass` (disparities [pass*dc, pass*dc + dc)) of every job that has it.
 // Pairs are bucketed by block size (warps per block) so no block carries
 // idle warps for a larger pair; one launch per bucket and stage.
+// The slice of one view (dstride words per pixel, pixel index y * W + x) for
+// the tile copies of k_vagg: a box of 36 words (the group's 32 disparities
+// and 4 words of padding) by 32 consecutive rows (row_scan: columns).  Rank
+// 4: dims (disparity within the group, group, x, y), the padding beyond the
+// 32-long dimension 0 is zero-filled without a read.  Rank 3 (used if the
+// encoder refuses a box wider than dimension 0): dims (disparity, x, y), the
+// padding reads the next group's first words (zeros past the last group).
+dco_status slice_map(dco_stereo *h, VArgs &a, int v, const uint32_t *slice, int W, int H, int dstride, bool row_scan)
+{
+    static int rank = 4;   // the encoder's answer for rank 4, kept for the process
+    TmapEncode enc = tmap_encoder();
+    if (!enc) {
+        h->last_error = "cuTensorMapEncodeTiled is not available";
+        return DCO_ECUDA;
+    }
+    const cuuint32_t rows = row_scan ? 1u : (cuuint32_t)kVSeg, cols = row_scan ? (cuuint32_t)kVSeg : 1u;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = CUDA_ERROR_INVALID_VALUE;
+    if (rank == 4) {
+        const cuuint64_t dims[4] = {32, (cuuint64_t)(dstride / 32), (cuuint64_t)W, (cuuint64_t)H};
+        const cuuint64_t strides[3] = {128, (cuuint64_t)dstride * 4, (cuuint64_t)W * dstride * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)kQS, 1, cols, rows};
+        r = enc(&a.tm[v], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<uint32_t *>(slice), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) rank = 3;
+    }
+    if (rank == 3) {
+        const cuuint64_t dims[3] = {(cuuint64_t)dstride, (cuuint64_t)W, (cuuint64_t)H};
+        const cuuint64_t strides[2] = {(cuuint64_t)dstride * 4, (cuuint64_t)W * dstride * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)kQS, cols, rows};
+        r = enc(&a.tm[v], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t *>(slice), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) {
+        h->last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return DCO_ECUDA;
+    }
+    a.tm_rank = rank;
+    return DCO_OK;
+}
+
 dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> &jobs, int pass, cudaStream_t s)
 {
     std::map<int, std::vector<Item<HArgs>>> hb;
@@ -1481,7 +1633,11 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         b.a.vol = j.vol; b.a.vol_view = j.vol_view;
         b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
-        b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        for (int v = 0; v < 2; v++) {
+            dco_status st = slice_map(h, b.a, v, b.a.sh[v], j.W, j.H, j.L.dstride, vh);
+            if (st != DCO_OK) return st;
+        }
         b.gx = vg.grid.x; b.gy = vg.grid.y; b.gz = vg.grid.z;
         vb[vg.nw].push_back(b);
     }
@@ -1500,9 +1656,9 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         if (st != DCO_OK) return st;
     }
     for (auto &kv : vb) {
-        dco_status st = vh ? launch_items(h, s, "k_hwta", k_vagg<1, false, true>, k_vagg<kBatchMax, false, true>,
+        dco_status st = vh ? launch_items(h, s, "k_hwta", k_vagg<1, false, true>, k_vagg<kVBatch, false, true>,
                                           kv.second, kv.first * 32, vsm[kv.first])
-                           : launch_items(h, s, "k_vagg", k_vagg<1, false>, k_vagg<kBatchMax, false>, kv.second,
+                           : launch_items(h, s, "k_vagg", k_vagg<1, false>, k_vagg<kVBatch, false>, kv.second,
                                           kv.first * 32, vsm[kv.first]);
         if (st != DCO_OK) return st;
     }
@@ -1550,7 +1706,9 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
         b.a.mask = j.vsrc;
         b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
-        b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        if (dco_status st = slice_map(h, b.a, 0, b.a.sh[0], j.W, j.H, j.L.dstride, false); st != DCO_OK) return st;
+        b.a.tm[1] = b.a.tm[0];
         b.gx = vg.grid.x; b.gy = 1; b.gz = vg.grid.z;   // the left view only
         vb[vg.nw].push_back(b);
     }
@@ -1560,7 +1718,7 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
         if (st != DCO_OK) return st;
     }
     for (auto &kv : vb) {
-        dco_status st = launch_items(h, s, "k_vvote", k_vagg<1, true>, k_vagg<kBatchMax, true>, kv.second,
+        dco_status st = launch_items(h, s, "k_vvote", k_vagg<1, true>, k_vagg<kVBatch, true>, kv.second,
                                      kv.first * 32, vsm[kv.first]);
         if (st != DCO_OK) return st;
     }

@@ -18,6 +18,7 @@
 // rounded per-pixel costs; only the Eq. 1 evaluation (FP32) and the rounding
 // to fixed point differ from the real-valued definition.
 #pragma once
+#include <cuda.h>   // CUtensorMap (the encoder is reached through the runtime)
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -110,6 +111,10 @@ struct SmoothArgs {
 };
 
 struct VArgs {
+    // per view: the slice as a TMA tile map (dims: disparity within the
+    // group, group, x, y; box: the group's 32 disparities plus 4 zero-filled
+    // words, of 32 consecutive scan positions)
+    CUtensorMap tm[2];
     const uint32_t *sh[2];
     const uchar4 *arms[2];
     unsigned long long *best[2];
@@ -117,6 +122,8 @@ struct VArgs {
     float *cost[2];
     float *vol;            // optional (D, H, W) normalised costs of view `vol_view`
     const int16_t *mask;   // optional: pixels where mask < 0 are written as -1 (vote)
+    int *status;           // device status word (a lost tile copy sets a bit)
+    int tm_rank;           // 4: tm as above; 3: dims (disparity, x, y), box 36 x 1 x 32 at (32 g, x, y)
     int vol_view;
     int W, H, D;
     int d0, dc, dstride;
