@@ -30,8 +30,11 @@
  *     Limits: 1 <= W, H <= 16384; 1 <= D <= 256; D <= W; 1 <= arm_l1 <= 40;
  *     census window odd, at most 64 bits; lambda_ad, lambda_census, eps > 0;
  *     gamma_l >= 0.
- *   - Device-side failures (an internal bound check) do not trap: they set
- *     the handle's status word, read with dco_stereo_sync_status().
+ *   - Device-side failures do not trap: they set the handle's status word,
+ *     read with dco_stereo_sync_status() (DCO_EDEVICE).  The vertical pass
+ *     sets bit 0 when a TMA tile copy does not complete within its bounded
+ *     mbarrier wait and bit 1 when its shared memory is not 128-byte aligned
+ *     for the copies; the pass's outputs are then not valid.
  */
 #ifndef DCO_STEREO_H
 #define DCO_STEREO_H
@@ -328,6 +331,9 @@ dco_status dco_stereo_sync_status(dco_stereo *h);
  *     nothing in it needs to start at zero (every word a kernel reads was
  *     written earlier in the same call).  Calls that overlap on the GPU
  *     (other streams, other threads) race on it: serialise them.
+ *   - A device-side failure (see the status word above) lands in a word of
+ *     the array; with no handle it is not reported, and disp_out is then
+ *     not valid.
  * left, right: device W*H*3 bytes; disp_out: device W*H int16; p = NULL
  * uses the defaults (p->d_chunk is ignored).
  */

@@ -613,9 +613,11 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
 //   0. every warp moves its 32 slice rows (128 bytes each: the group's
 //      disparities of one pixel) into Q[y - ya] with one TMA tile copy
 //      (completing on the warp's mbarrier);
-//   A. lane = disparity: the segment sum, exchanged with the other warps,
-//      then the column prefix (with its segment offset) written back in
-//      place;
+//   A. lane = disparity: the warp's 32 tile rows into registers, the
+//      segment sum exchanged with the other warps, then the column prefix
+//      (with its segment offset) written back in place (the rows of a
+//      partial tile past the range are summed after the range's last row,
+//      and the last warp's total is read by no other warp);
 //   C. lane = output row: V(d) = Q(y + dn, d) - Q(y - up - 1, d) for the 32
 //      disparities (Eq. 2: the sum over the vertical arm of the horizontal
 //      sums; N does not depend on d, so the WTA compares V), running minimum
@@ -710,7 +712,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     uint32_t *NT = NQ + len;                  // [nw]
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(vsmem) + 4u * (uint32_t)vagg_bar_word(len, nw) + 8u * warp;
     if (((uint32_t)__cvta_generic_to_shared(Q) & 127u) != 0) {   // the tile copies need 128-byte alignment
-        if (threadIdx.x == 0) atomicOr(a.status, kStatusAlign);
+        if (threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusAlign);
         return;
     }
 
@@ -769,12 +771,9 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         if (nrow > 0 && !mbar_wait(bar, (uint32_t)(g & 1))) lost = true;
         uint32_t *q = Q + sa * kQS + lane;
         uint32_t tot = 0;
-        if (nrow == kVSeg) {
-#pragma unroll 8
-            for (int u = 0; u < kVSeg; u++) tot += q[u * kQS];
-        } else {
-            for (int u = 0; u < nrow; u++) tot += q[u * kQS];
-        }
+        uint32_t v[kVSeg];
+#pragma unroll
+        for (int u = 0; u < kVSeg; u++) { v[u] = q[u * kQS]; tot += v[u]; }
         T[warp * 32 + lane] = tot;
         __syncthreads();
         uint32_t run = 0;
@@ -785,17 +784,10 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
             for (int w = 0; w < warp; w++) noff += NT[w];
             if (rin) NQ[r] += noff;
         }
-        if (nrow == kVSeg) {
-#pragma unroll 8
-            for (int u = 0; u < kVSeg; u++) {
-                run += q[u * kQS];
-                q[u * kQS] = run;
-            }
-        } else {
-            for (int u = 0; u < nrow; u++) {
-                run += q[u * kQS];
-                q[u * kQS] = run;
-            }
+#pragma unroll
+        for (int u = 0; u < kVSeg; u++) {
+            run += v[u];
+            q[u * kQS] = run;
         }
         __syncthreads();
         // ---- C: lane = output row, loop over the group's disparities
@@ -842,7 +834,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     if (lost) {
         // a copy never completed: report, and give the others in flight a
         // last bounded wait before the block's shared memory is released
-        if (lane == 0) atomicOr(a.status, kStatusCopyTimeout);
+        if (lane == 0 && a.status) atomicOr(a.status, kStatusCopyTimeout);
         mbar_wait(bar, (uint32_t)((ng - 1) & 1));
         return;
     }
@@ -985,7 +977,7 @@ __global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __g
 }
 
 template <int N, bool kMax, bool kRow = false>
-__global__ void __launch_bounds__(16 * 32, 3) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
+__global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
 {
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
@@ -2414,9 +2406,11 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     p.d_chunk = 32;   // passes of 32 disparities keep the slices small
     Derived dv;
     derive(p, dv);
-    const size_t tab_bytes = align_up(sizeof(float) * kTabFloats);
+    // scratch: tables, a status word (kernel checks land there; this entry
+    // point has no handle to report them through), the workspace
+    const size_t tab_bytes = align_up(sizeof(float) * kTabFloats), status_bytes = align_up(sizeof(int));
     const Layout L = make_layout(W, H, D, p);
-    if (tab_bytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
+    if (tab_bytes + status_bytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DCO_ECUDA;
     void *base = nullptr;
@@ -2432,8 +2426,9 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     // a handle that owns nothing: its workspace and tables are the scratch
     dco_stereo view;
     view.device = dev;
-    view.ws = static_cast<char *>(base) + tab_bytes;
-    view.ws_cap = kNoAllocScratchBytes - tab_bytes;
+    view.d_status = reinterpret_cast<int *>(static_cast<char *>(base) + tab_bytes);
+    view.ws = static_cast<char *>(base) + tab_bytes + status_bytes;
+    view.ws_cap = kNoAllocScratchBytes - tab_bytes - status_bytes;
     view.d_tables = static_cast<float *>(base);
     view.tab_valid = true;
     view.tab_key[0] = p.lambda_ad;
@@ -2444,5 +2439,6 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     st = run_match(&view, left, right, W, H, D, p, disp_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0, s);
     view.ws = nullptr;
     view.d_tables = nullptr;
+    view.d_status = nullptr;
     return st;
 }
