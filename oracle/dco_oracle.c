@@ -35,6 +35,19 @@
  *     segment) is available as a variant.
  *   - d in [0, D-1]; a match outside the image costs 1 (upper bound of Eq. 1).
  *   - WTA (Eq. 3) takes the smallest d among equal minima.
+ *   - the decision in the kernel's precision (optional outputs qdisp_*):
+ *     the paper fixes no precision, so where floating point decides the
+ *     argmin the oracle can also take it as the GPU does: lambda_AD,
+ *     lambda_census, gamma_L and eps rounded to FP32; the tables
+ *     T_AD[k] = 1 - exp(-(k/3)/lambda_AD) (k = channel sum 0..765),
+ *     T_cen[h] = 1 - exp(-h/lambda_census) (h = 0..64) and
+ *     alphaS[l] = alpha(l) * S evaluated in FP64 and rounded to FP32 once;
+ *     the cost of Eq. 1 in FP32 as fma(alphaS, T_AD[k], (S - alphaS) *
+ *     T_cen[h]) (one rounding per operation), rounded to the nearest
+ *     integer (ties to even) at the fixed-point scale
+ *     S = floor((2^32 - 1) / (2 L1 + 1)^2) - 1, a match outside the image
+ *     costing S; the region sums of these integers are exact and the
+ *     smallest sum wins, the smallest d among equal sums.
  *   - outlier removal: left-right consistency, valid iff x - dL >= 0 and
  *     |dL(x) - dR(x - dL)| <= tol, otherwise -1.
  *   - parallax optimisation (Sect. 4.3, Eq. 4), applied to the checked map:
@@ -210,7 +223,31 @@ typedef struct {
     int sign;                           /* -1: left reference (q = p - d); +1: right */
     orc_cost_params cp;
     int order;                          /* 0: region H then V (Eq. 2 reading); 1: V then H */
+    /* the decision in the kernel's precision (see the header) */
+    float q_ad[766], q_cen[65], q_as[64];
+    float qS;
+    uint32_t qSint;
 } view_ctx;
+
+/* fixed-point scale: the largest full region ((2 L1 + 1)^2 costs <= 1) fits
+   in 32 bits, with one unit of margin */
+static uint32_t fixed_scale(int L1)
+{
+    uint64_t n = (uint64_t)(2 * L1 + 1) * (uint64_t)(2 * L1 + 1);
+    return (uint32_t)(0xffffffffull / n - 1);
+}
+
+/* the FP32 tables of Eq. 1 with the parameters rounded to FP32 */
+static void quant_tables(view_ctx *v, int L1)
+{
+    double lad = (double)(float)v->cp.lambda_ad, lcen = (double)(float)v->cp.lambda_census;
+    double gam = (double)(float)v->cp.gamma_l, eps = (double)(float)v->cp.eps;
+    v->qSint = fixed_scale(L1);
+    v->qS = (float)v->qSint;
+    for (int k = 0; k <= 765; k++) v->q_ad[k] = (float)(1.0 - exp(-((double)k / 3.0) / lad));
+    for (int h = 0; h <= 64; h++) v->q_cen[h] = (float)(1.0 - exp(-(double)h / lcen));
+    for (int l = 0; l < 64; l++) v->q_as[l] = (float)((1.0 - exp(-gam / ((double)l + eps))) * (double)v->qSint);
+}
 
 static int lmin_of(const uint8_t *a)
 {
@@ -231,6 +268,22 @@ static double pixel_cost(const view_ctx *v, int x, int y, int d)
     int lmin = lmin_of(v->ref_arms + 4 * ip);
     return orc_cost_terms(ad, ham, lmin, v->cp.lambda_ad, v->cp.lambda_census,
                           v->cp.gamma_l, v->cp.eps);
+}
+
+/* the same cost in the kernel's precision, as an integer at scale S */
+static uint32_t pixel_qcost(const view_ctx *v, int x, int y, int d)
+{
+    int xo = x + v->sign * d;
+    if (xo < 0 || xo >= v->W) return v->qSint;
+    long ip = (long)y * v->W + x, io = (long)y * v->W + xo;
+    const uint8_t *a = v->ref_rgb + 3 * ip, *b = v->oth_rgb + 3 * io;
+    int ad = abs((int)a[0] - (int)b[0]) + abs((int)a[1] - (int)b[1]) + abs((int)a[2] - (int)b[2]);
+    int ham = orc_hamming(v->ref_cen[ip], v->oth_cen[io]);
+    float as = v->q_as[lmin_of(v->ref_arms + 4 * ip)];
+    float rest = v->qS - as;               /* FP32 difference */
+    float cen = rest * v->q_cen[ham];      /* FP32 product */
+    float c = fmaf(as, v->q_ad[ad], cen);  /* one rounding */
+    return (uint32_t)nearbyintf(c);        /* nearest integer, ties to even */
 }
 
 /* Eq. 2 support-region size N of pixel (x, y): order 0 sums, over q on p's
@@ -263,7 +316,7 @@ static long region_size(const view_ctx *v, int x, int y)
  * aggregated cost; optionally the whole aggregated volume [d][y-y0][x].
  */
 static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
-                    double *best, double *second, double *vol)
+                    double *best, double *second, double *vol, int16_t *qdisp)
 {
     int W = v->W, H = v->H;
     int ya = y0 - reach < 0 ? 0 : y0 - reach;
@@ -272,15 +325,29 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
     double *C = (double *)malloc(sizeof(double) * (size_t)W * nr);
     double *SH = (double *)malloc(sizeof(double) * (size_t)W * nr);
     long *N = (long *)malloc(sizeof(long) * (size_t)W * no);
-    if (!C || !SH || !N) { free(C); free(SH); free(N); return ORC_ENOMEM; }
+    /* kernel-precision decision: integer costs, their segment sums, the best sum */
+    uint32_t *QC = qdisp ? (uint32_t *)malloc(sizeof(uint32_t) * (size_t)W * nr) : NULL;
+    uint64_t *QH = qdisp ? (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * nr) : NULL;
+    uint64_t *qbest = qdisp ? (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * no) : NULL;
+    if (!C || !SH || !N || (qdisp && (!QC || !QH || !qbest))) {
+        free(C); free(SH); free(N); free(QC); free(QH); free(qbest);
+        return ORC_ENOMEM;
+    }
     for (int y = y0; y < y1; y++)
         for (int x = 0; x < W; x++) N[(long)(y - y0) * W + x] = region_size(v, x, y);
     for (long i = 0; i < (long)W * no; i++) { best[i] = INFINITY; second[i] = INFINITY; disp[i] = 0; }
+    if (qdisp)
+        for (long i = 0; i < (long)W * no; i++) { qbest[i] = UINT64_MAX; qdisp[i] = 0; }
 
     for (int d = 0; d < v->D; d++) {
 #pragma omp parallel for schedule(static)
         for (int y = ya; y < yb; y++)
             for (int x = 0; x < W; x++) C[(long)(y - ya) * W + x] = pixel_cost(v, x, y, d);
+        if (qdisp) {
+#pragma omp parallel for schedule(static)
+            for (int y = ya; y < yb; y++)
+                for (int x = 0; x < W; x++) QC[(long)(y - ya) * W + x] = pixel_qcost(v, x, y, d);
+        }
         if (v->order == 0) {
             /* segment sums along each row (q's horizontal segment) */
 #pragma omp parallel for schedule(static)
@@ -290,6 +357,11 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
                     double s = 0.0;
                     for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += C[(long)(y - ya) * W + xx];
                     SH[(long)(y - ya) * W + x] = s;
+                    if (qdisp) {
+                        uint64_t qs = 0;
+                        for (int xx = x - a[0]; xx <= x + a[1]; xx++) qs += QC[(long)(y - ya) * W + xx];
+                        QH[(long)(y - ya) * W + x] = qs;
+                    }
                 }
             }
         } else {
@@ -301,6 +373,11 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
                     double s = 0.0;
                     for (int yy = y - a[2]; yy <= y + a[3]; yy++) s += C[(long)(yy - ya) * W + x];
                     SH[(long)(y - ya) * W + x] = s;
+                    if (qdisp) {
+                        uint64_t qs = 0;
+                        for (int yy = y - a[2]; yy <= y + a[3]; yy++) qs += QC[(long)(yy - ya) * W + x];
+                        QH[(long)(y - ya) * W + x] = qs;
+                    }
                 }
             }
         }
@@ -318,10 +395,19 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
                 if (vol) vol[(long)d * W * no + i] = cbar;
                 if (cbar < best[i]) { second[i] = best[i]; best[i] = cbar; disp[i] = (int16_t)d; }
                 else if (cbar < second[i]) { second[i] = cbar; }
+                if (qdisp) {
+                    /* exact integer region sum; N does not depend on d */
+                    uint64_t qs = 0;
+                    if (v->order == 0)
+                        for (int yy = y - a[2]; yy <= y + a[3]; yy++) qs += QH[(long)(yy - ya) * W + x];
+                    else
+                        for (int xx = x - a[0]; xx <= x + a[1]; xx++) qs += QH[(long)(y - ya) * W + xx];
+                    if (qs < qbest[i]) { qbest[i] = qs; qdisp[i] = (int16_t)d; }
+                }
             }
         }
     }
-    free(C); free(SH); free(N);
+    free(C); free(SH); free(N); free(QC); free(QH); free(qbest);
     return ORC_OK;
 }
 
@@ -349,7 +435,9 @@ int orc_lr_check(const int16_t *dl, const int16_t *dr, int W, int rows, int tol,
  * Full matcher on rows [y0, y1) of a W x H pair with D disparities.
  * Every output array holds (y1 - y0) x W values; vol_l / vol_r (optional)
  * hold D x (y1 - y0) x W aggregated costs.  Census and arms are computed on
- * the whole image (they are cheap next to the aggregation).
+ * the whole image (they are cheap next to the aggregation).  qdisp_l /
+ * qdisp_r (optional, both or neither) receive the Eq. 3 decisions taken in
+ * the kernel's precision (header); disp_* are the FP64 decisions.
  */
 int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
               double lambda_ad, double lambda_census, double gamma_l, double eps,
@@ -357,7 +445,7 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
               int y0, int y1,
               int16_t *disp_l, int16_t *disp_r, int16_t *disp_final,
               double *best_l, double *second_l, double *best_r, double *second_r,
-              double *vol_l, double *vol_r)
+              double *vol_l, double *vol_r, int16_t *qdisp_l, int16_t *qdisp_r)
 {
     if (!left || !right || W < 1 || H < 1 || D < 1 || y0 < 0 || y1 > H || y0 > y1) return ORC_EINVAL;
     if (!disp_l || !disp_r || !disp_final || !best_l || !second_l || !best_r || !second_r)
@@ -377,10 +465,16 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
     }
     {
         orc_cost_params cp = {lambda_ad, lambda_census, gamma_l, eps};
-        view_ctx vl = {W, H, D, left, right, cl, cr, al, -1, cp, order};
-        view_ctx vr = {W, H, D, right, left, cr, cl, ar, +1, cp, order};
-        if ((rc = run_view(&vl, y0, y1, L1, disp_l, best_l, second_l, vol_l)) != ORC_OK) goto done;
-        if ((rc = run_view(&vr, y0, y1, L1, disp_r, best_r, second_r, vol_r)) != ORC_OK) goto done;
+        view_ctx *vl = (view_ctx *)calloc(1, sizeof(view_ctx)), *vr = (view_ctx *)calloc(1, sizeof(view_ctx));
+        if (!vl || !vr) { free(vl); free(vr); rc = ORC_ENOMEM; goto done; }
+        *vl = (view_ctx){W, H, D, left, right, cl, cr, al, -1, cp, order};
+        *vr = (view_ctx){W, H, D, right, left, cr, cl, ar, +1, cp, order};
+        if (qdisp_l && qdisp_r) { quant_tables(vl, L1); quant_tables(vr, L1); }
+        rc = run_view(vl, y0, y1, L1, disp_l, best_l, second_l, vol_l, qdisp_l && qdisp_r ? qdisp_l : NULL);
+        if (rc == ORC_OK)
+            rc = run_view(vr, y0, y1, L1, disp_r, best_r, second_r, vol_r, qdisp_l && qdisp_r ? qdisp_r : NULL);
+        free(vl); free(vr);
+        if (rc != ORC_OK) goto done;
         rc = orc_lr_check(disp_l, disp_r, W, y1 - y0, lr_tol, disp_final);
     }
 done:

@@ -41,7 +41,7 @@ def lib():
         L.orc_cost_terms.argtypes = [i, i, i, d, d, d, d]
         L.orc_cost_terms.restype = d
         L.orc_lr_check.argtypes = [P, P, i, i, i, P]
-        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i, i] + [P] * 9
+        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i, i] + [P] * 11
         L.orc_arms_smooth.argtypes = [P, i, i, P]
         L.orc_arms_smooth.restype = i
         L.orc_vote.argtypes = [P, P, i, i, i, i, P]
@@ -195,10 +195,19 @@ class MatchResult:
     vol_l: Optional[np.ndarray] = None   # (D, rows, W) aggregated costs
     vol_r: Optional[np.ndarray] = None
     y0: int = 0
+    # Eq. 3 decisions taken in the kernel's precision (FP32 Eq. 1, fixed
+    # point at scale S, exact integer region sums); None unless requested
+    qdisp_l: Optional[np.ndarray] = None
+    qdisp_r: Optional[np.ndarray] = None
+    qdisp: Optional[np.ndarray] = None   # LR check of qdisp_l, qdisp_r
 
 
 def match(left: np.ndarray, right: np.ndarray, D: int, p: Params = Params(),
-          rows: Optional[tuple[int, int]] = None, volume: bool = False) -> MatchResult:
+          rows: Optional[tuple[int, int]] = None, volume: bool = False,
+          quantized: bool = False) -> MatchResult:
+    """Eqs. 1-3 for both reference views and the LR check on rows [y0, y1).
+    quantized: also the Eq. 3 decisions in the kernel's precision (the paper
+    fixes none; see the oracle's header for the recipe)."""
     left = _rgb(left)
     right = _rgb(right)
     H, W, _ = left.shape
@@ -212,13 +221,17 @@ def match(left: np.ndarray, right: np.ndarray, D: int, p: Params = Params(),
     br = np.empty((n, W)); sr = np.empty((n, W))
     vl = np.empty((D, n, W)) if volume else None
     vr = np.empty((D, n, W)) if volume else None
+    ql = np.empty((n, W), np.int16) if quantized else None
+    qr = np.empty((n, W), np.int16) if quantized else None
     null = ctypes.c_void_p(0)
     _check(lib().orc_match(_ptr(left), _ptr(right), W, H, D, p.lambda_ad, p.lambda_census,
                            p.gamma_l, p.eps, p.census_w, p.census_h, p.arm_l1, p.arm_l2,
                            p.tau1, p.tau2, p.lr_tol, p.smooth_arms, p.agg_order, y0, y1,
                            _ptr(dl), _ptr(dr), _ptr(df), _ptr(bl), _ptr(sl), _ptr(br), _ptr(sr),
-                           _ptr(vl) if volume else null, _ptr(vr) if volume else null))
-    return MatchResult(dl, dr, df, bl, sl, br, sr, vl, vr, y0)
+                           _ptr(vl) if volume else null, _ptr(vr) if volume else null,
+                           _ptr(ql) if quantized else null, _ptr(qr) if quantized else null))
+    qf = lr_check(ql, qr, p.lr_tol) if quantized else None
+    return MatchResult(dl, dr, df, bl, sl, br, sr, vl, vr, y0, ql, qr, qf)
 
 
 def set_threads(n: int) -> None:

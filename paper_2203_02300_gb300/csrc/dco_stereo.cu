@@ -192,11 +192,17 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     const uint32_t k2 = 0x00100401u * (uint32_t)(min(a.tau2, 255) + 511);
     const uint32_t ep = p;   // colours are stored spread (k_pack)
     const uint32_t K1p = k1 - ep, pK1 = ep + k1, K2p = k2 - ep, pK2 = ep + k2;
-    // step j fails: far from p or from its predecessor (tau1), or beyond L2
-    // and far from p (tau2)
+    // step j fails: far from its predecessor (tau1), far from p (tau1), or
+    // beyond L2 and far from p (tau2; with tau2 <= tau1 that test implies
+    // the tau1 test against p, which is then skipped)
+    const bool t2_implies_t1 = a.tau2 <= a.tau1;
     auto fails = [&](uint32_t ec, uint32_t eq, int j) -> bool {
-        if (use1 && (!within(ec, K1p, pK1) || !within(ec, k1 - eq, eq + k1))) return true;
-        return j > L2 && use2 && !within(ec, K2p, pK2);
+        if (use1 && !within(ec, k1 - eq, eq + k1)) return true;
+        if (j > L2 && use2) {
+            if (!within(ec, K2p, pK2)) return true;
+            return !t2_implies_t1 && use1 && !within(ec, K1p, pK1);
+        }
+        return use1 && !within(ec, K1p, pK1);
     };
     // the first kArmBatch candidates of all four directions are loaded at
     // once (in-image addresses only), so a typical pixel pays one load latency

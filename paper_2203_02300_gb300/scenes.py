@@ -11,6 +11,13 @@ This module is the only code shared by the oracle tests, the GPU tests and
 the benchmark.  It draws random numbers and builds images; it holds none of
 the matcher's arithmetic (no census, arm, cost, aggregation or WTA step).
 
+Two albedo recipes: "fine" (uniform noise blurred with sigma 1: busy
+texture, arms of one or two pixels) and "mixed" (per surface a base colour,
+smooth shading and fine texture of a contrast from nearly flat to busy, as
+on the walls, floors and objects of indoor frames: at 640x480 the arms
+average 4 pixels, median 2, 90th percentile 17, longest 33).  Config 1 uses
+"fine", configs 2-5 "mixed".
+
 Workload recipes (seed = 2203_02300 + 1000*config + item):
   1  320x240, D=32, 4-8 fronto-parallel planes, d in [2,30], no noise.
   2  640x480, D=64, 12 slanted planes (|dd/dx|,|dd/dy| <= 0.2), d in [2,60],
@@ -62,6 +69,33 @@ def _texture(rng: np.random.Generator, h: int, w: int) -> np.ndarray:
     return blurred
 
 
+# standard deviation (grey levels) of a surface's fine texture in the mixed
+# recipe: from nearly flat (walls, floors: long arms) to busy
+MIXED_CONTRAST = (2.0, 5.0, 12.0, 30.0)
+
+
+def _mixed_texture(rng: np.random.Generator, h: int, w: int) -> np.ndarray:
+    """Indoor-like albedo of one surface: a base colour (uniform in [40, 215]
+    per channel), smooth shading (standard-normal noise on a grid of one node
+    per 32 pixels, cubic-interpolated, scaled to a standard deviation of 10
+    levels) and fine texture (standard-normal noise blurred with sigma 1,
+    scaled to a contrast drawn from MIXED_CONTRAST)."""
+    base = rng.uniform(40.0, 215.0, size=3).astype(np.float32)
+    contrast = float(MIXED_CONTRAST[int(rng.integers(0, len(MIXED_CONTRAST)))])
+    gh, gw = h // 32 + 2, w // 32 + 2
+    coarse = rng.standard_normal((gh, gw, 3)).astype(np.float32)
+    low = ndimage.zoom(coarse, (h / gh, w / gw, 1.0), order=3, mode="reflect", grid_mode=True)[:h, :w]
+    low = low * (10.0 / (float(low.std()) + 1e-6))
+    fine = ndimage.gaussian_filter(rng.standard_normal((h, w, 3)).astype(np.float32), sigma=(1.0, 1.0, 0.0),
+                                   truncate=3.0, mode="reflect")
+    fine = fine * (contrast / (float(fine.std()) + 1e-6))
+    return base + low + fine
+
+
+def _albedo(kind: str):
+    return _mixed_texture if kind == "mixed" else _texture
+
+
 @dataclasses.dataclass
 class _Surface:
     x0: int
@@ -73,7 +107,7 @@ class _Surface:
     c: float = 0.0           # disparity at the box centre
 
 
-def _rect(rng, W, H, dlo, dhi, slanted, slope):
+def _rect(rng, W, H, dlo, dhi, slanted, slope, texture="fine"):
     w = int(rng.integers(max(2, W // 8), max(3, W // 2) + 1))
     h = int(rng.integers(max(2, H // 8), max(3, H // 2) + 1))
     x0 = int(rng.integers(-w // 4, W - (3 * w) // 4 + 1))
@@ -81,20 +115,20 @@ def _rect(rng, W, H, dlo, dhi, slanted, slope):
     c = float(rng.integers(dlo, dhi + 1)) if not slanted else float(rng.uniform(dlo, dhi))
     a = float(rng.uniform(-slope, slope)) if slanted else 0.0
     b = float(rng.uniform(-slope, slope)) if slanted else 0.0
-    return _Surface(x0, y0, _texture(rng, h, w), np.ones((h, w), bool), a, b, c)
+    return _Surface(x0, y0, _albedo(texture)(rng, h, w), np.ones((h, w), bool), a, b, c)
 
 
-def _disc(rng, W, H, dlo, dhi):
+def _disc(rng, W, H, dlo, dhi, texture="fine"):
     r = int(rng.integers(3, 13))
     cx = int(rng.integers(0, W))
     cy = int(rng.integers(0, H))
     yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
     mask = (xx * xx + yy * yy) <= r * r
     c = float(rng.integers(dlo, dhi + 1))
-    return _Surface(cx - r, cy - r, _texture(rng, 2 * r + 1, 2 * r + 1), mask, 0.0, 0.0, c)
+    return _Surface(cx - r, cy - r, _albedo(texture)(rng, 2 * r + 1, 2 * r + 1), mask, 0.0, 0.0, c)
 
 
-def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset):
+def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset, texture="fine"):
     """Z-buffer the surfaces into the left view, forward-warp to the right view."""
     disp = np.full((H, W), -1.0, np.float32)
     left = np.zeros((H, W, 3), np.float32)
@@ -122,7 +156,7 @@ def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset):
     key = np.full((H, W), -1, np.int64)
     k_src = di * W + xs
     np.maximum.at(key, (ys[inb], xr[inb]), k_src[inb])
-    right = _texture(rng, H, W)                 # fresh texture fills the holes
+    right = _albedo(texture)(rng, H, W)         # fresh texture fills the holes
     filled = key >= 0
     src_x = key[filled] % W
     right[filled] = left[ys[filled], src_x]
@@ -145,19 +179,20 @@ def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset):
 def plane_scene(W: int, H: int, D: int, n_planes: int, seed: int, *,
                 slanted: bool = False, slope: float = 0.2, noise_sigma: float = 0.0,
                 gain: float = 1.0, offset: float = 0.0, n_discs: int = 0,
-                disc_range=(160, 250), drange=None) -> Scene:
-    """A background plane plus `n_planes` rectangles (and optional discs)."""
+                disc_range=(160, 250), drange=None, texture: str = "fine") -> Scene:
+    """A background plane plus `n_planes` rectangles (and optional discs);
+    texture "fine" (blurred uniform noise) or "mixed" (indoor-like)."""
     rng = np.random.default_rng(seed)
     dlo, dhi = drange if drange is not None else (2, max(2, min(D - 2, 60 if D <= 64 else D - 2)))
-    bg = _Surface(0, 0, _texture(rng, H, W), np.ones((H, W), bool),
+    bg = _Surface(0, 0, _albedo(texture)(rng, H, W), np.ones((H, W), bool),
                   0.0, 0.0, float(dlo))
     surfaces = [bg]
     for _ in range(n_planes):
-        surfaces.append(_rect(rng, W, H, dlo, dhi, slanted, slope))
+        surfaces.append(_rect(rng, W, H, dlo, dhi, slanted, slope, texture))
     for _ in range(n_discs):
-        surfaces.append(_disc(rng, W, H, *disc_range))
+        surfaces.append(_disc(rng, W, H, *disc_range, texture=texture))
     left, right, disp, occ = _render(W, H, surfaces, (dlo, dhi if not n_discs else max(dhi, disc_range[1])),
-                                     rng, noise_sigma, gain, offset)
+                                     rng, noise_sigma, gain, offset, texture)
     return Scene(left, right, disp, occ, D)
 
 
@@ -170,15 +205,15 @@ def config_scene(config: int, item: int = 0) -> Scene:
         return plane_scene(320, 240, 32, n, seed + 7, drange=(2, 30))
     if config == 2:
         return plane_scene(640, 480, 64, 12, seed + 7, slanted=True, slope=0.2,
-                           noise_sigma=2.0, gain=1.03, offset=5.0, drange=(2, 60))
+                           noise_sigma=2.0, gain=1.03, offset=5.0, drange=(2, 60), texture="mixed")
     if config == 3:
         sizes = [(320, 240, 32), (640, 480, 64), (960, 540, 128), (1280, 720, 128)]
         W, H, D = sizes[int(rng.integers(0, 4))]
         n = int(rng.integers(4, 17))
-        return plane_scene(W, H, D, n, seed + 7, noise_sigma=2.0, drange=(2, D - 2))
+        return plane_scene(W, H, D, n, seed + 7, noise_sigma=2.0, drange=(2, D - 2), texture="mixed")
     if config == 5:
         return plane_scene(1920, 1080, 256, 32, seed + 7, noise_sigma=3.0,
-                           n_discs=200, disc_range=(160, 250), drange=(2, 150))
+                           n_discs=200, disc_range=(160, 250), drange=(2, 150), texture="mixed")
     raise ValueError(f"config {config} has no single-scene recipe")
 
 
@@ -197,8 +232,8 @@ class StreamScene:
         self.seed = seed_for(4, stream)
         rng = np.random.default_rng(self.seed)
         self.dlo, self.dhi = 2, D - 2
-        self.bg = _texture(rng, H, W)
-        self.planes = [_rect(rng, W, H, self.dlo, self.dhi, False, 0.0) for _ in range(n_planes)]
+        self.bg = _mixed_texture(rng, H, W)
+        self.planes = [_rect(rng, W, H, self.dlo, self.dhi, False, 0.0, "mixed") for _ in range(n_planes)]
         self.vel = []
         for _ in range(n_planes):
             speed = rng.uniform(0.0, 3.0)
@@ -213,7 +248,7 @@ class StreamScene:
                                                 y0=p.y0 + int(round(vy * t))))
         rng = np.random.default_rng(self.seed * 7919 + t)
         left, right, disp, occ = _render(self.W, self.H, surfaces, (self.dlo, self.dhi),
-                                         rng, 2.0, 1.0, 0.0)
+                                         rng, 2.0, 1.0, 0.0, "mixed")
         return Scene(left, right, disp, occ, self.D)
 
 

@@ -65,11 +65,8 @@ def test_depth_matches_the_oracle_path_under_the_parity_rule(env):
     s = scenes.plane_scene(160, 120, 32, 5, seed=scenes.seed_for(2, 650), drange=(2, 28))
     dh = torch.empty((60, 80), dtype=torch.int16, device="cuda")
     st.depth(_dev(torch, s.left), _dev(torch, s.right), 16, F_PX, BASE, disp_half=dh)
-    ref = O.match(O.downscale(s.left), O.downscale(s.right), 16)
-    got = dh.cpu().numpy()
-    keep = (got >= 0) & (ref.disp >= 0)
-    parity.check_disparity(got[keep], ref.disp[keep], ref.best_l[keep], ref.second_l[keep], "half-size map")
-    assert ((got >= 0) != (ref.disp >= 0)).mean() <= 2 * parity.MAX_EXCUSED
+    ref = O.match(O.downscale(s.left), O.downscale(s.right), 16, quantized=True)
+    parity.check_final(dh.cpu().numpy(), ref, "half-size map")
 
 
 def test_depth_recovers_a_plane(env):

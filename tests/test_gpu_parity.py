@@ -51,10 +51,10 @@ def full_check(env, left, right, D, bp=None, rows=None):
     torch, binding, st = env
     op = oparams(bp) if bp is not None else O.Params()
     out, dl, dr, cl, cr = run_views(env, left, right, D, bp)
-    ref = O.match(left, right, D, op, rows=rows)
+    ref = O.match(left, right, D, op, rows=rows, quantized=True)
     sl = slice(*rows) if rows else slice(None)
-    n = parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity")
-    n += parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity")
+    n = parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
+    n += parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
     parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, "left cost")
     parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, "right cost")
     assert (out == O.lr_check(dl, dr, op.lr_tol)).all(), "consistency map"
@@ -242,10 +242,10 @@ def test_vh_order_config5_sampled_rows(env):
     bp = binding.Params.default(agg_order=1)
     out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D, bp)
     for rows in ((0, 6), (509, 515), (1074, 1080)):
-        ref = O.match(s.left, s.right, s.D, O.Params(agg_order=1), rows=rows)
+        ref = O.match(s.left, s.right, s.D, O.Params(agg_order=1), rows=rows, quantized=True)
         sl = slice(*rows)
-        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l)
-        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r)
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
         parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
         parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
 
@@ -257,10 +257,10 @@ def test_config5_sampled_rows(env):
     torch, binding, st = env
     out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
     for rows in ((0, 6), (537, 543), (1074, 1080)):
-        ref = O.match(s.left, s.right, s.D, rows=rows)
+        ref = O.match(s.left, s.right, s.D, rows=rows, quantized=True)
         sl = slice(*rows)
-        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l)
-        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r)
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
         parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
         parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
     assert (out == O.lr_check(dl, dr, 1)).all()

@@ -54,9 +54,8 @@ def test_two_calls_match_the_regular_entry_point(env):
         # same kernels on the same inputs: the consistency maps agree exactly
         # (tolerance of integer work); also within the oracle's parity rule
         assert np.array_equal(got, want)
-        ref = O.match(s.left, s.right, s.D)
-        keep = (got >= 0) & (ref.disp >= 0)
-        parity.check_disparity(got[keep], ref.disp[keep], ref.best_l[keep], ref.second_l[keep], "no-alloc")
+        ref = O.match(s.left, s.right, s.D, quantized=True)
+        parity.check_final(got, ref, "no-alloc")
 
 
 def test_sizes_beyond_the_array_are_rejected(env):
