@@ -184,25 +184,20 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
 
     // arms: largest k <= L1 whose steps all pass the double threshold
     const size_t i = (size_t)y * W + x;
-    const uint32_t p = __ldg(rgbx + i);
+    const uint32_t p = __ldg(rgbx + i);   // colours are stored spread (k_pack)
     const int L1 = a.L1, L2 = a.L2;
-    // a threshold >= 256 never stops an arm (channel differences are <= 255)
-    const bool use1 = a.tau1 < 256, use2 = a.tau2 < 256;
-    const uint32_t k1 = 0x00100401u * (uint32_t)(min(a.tau1, 255) + 511);   // tau - 1 + 512 per field
-    const uint32_t k2 = 0x00100401u * (uint32_t)(min(a.tau2, 255) + 511);
-    const uint32_t ep = p;   // colours are stored spread (k_pack)
-    const uint32_t K1p = k1 - ep, pK1 = ep + k1, K2p = k2 - ep, pK2 = ep + k2;
-    // step j fails: far from its predecessor (tau1), far from p (tau1), or
-    // beyond L2 and far from p (tau2; with tau2 <= tau1 that test implies
-    // the tau1 test against p, which is then skipped)
-    const bool t2_implies_t1 = a.tau2 <= a.tau1;
-    auto fails = [&](uint32_t ec, uint32_t eq, int j) -> bool {
-        if (use1 && !within(ec, k1 - eq, eq + k1)) return true;
-        if (j > L2 && use2) {
-            if (!within(ec, K2p, pK2)) return true;
-            return !t2_implies_t1 && use1 && !within(ec, K1p, pK1);
-        }
-        return use1 && !within(ec, K1p, pK1);
+    // K = t - 1 + 512 in each 10-bit field, t = min(tau, 256): the field of
+    // E(c) + K - E(q) has bit 9 set exactly when c - q > -t, and with t = 256
+    // every pair passes (a threshold of 256 or more never stops an arm).
+    // Up to L2 a step is tested against p with tau1; beyond L2 against p
+    // with min(tau1, tau2) (both must hold); always against its predecessor
+    // with tau1.  One test covers both comparisons, the predecessor's
+    // constants carried from the previous step.
+    auto kfield = [](int tau) { return 0x00100401u * (uint32_t)(min(tau, 256) + 511); };
+    const uint32_t k1 = kfield(a.tau1), k2 = kfield(min(a.tau1, a.tau2));
+    const uint32_t K1p = k1 - p, pK1 = p + k1, K2p = k2 - p, pK2 = p + k2;
+    auto pass = [](uint32_t c, uint32_t Kp, uint32_t pK, uint32_t kq, uint32_t qk) {
+        return ((c + Kp) & (pK - c) & (c + kq) & (qk - c) & kM9) == kM9;
     };
     // the first kArmBatch candidates of all four directions are loaded at
     // once (in-image addresses only), so a typical pixel pays one load latency
@@ -222,25 +217,42 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     }
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        uint32_t prev = p;
+        uint32_t kq = k1 - p, qk = p + k1;   // predecessor constants (p itself before step 1)
         int n = 0;
         bool open = true;
 #pragma unroll
         for (int u = 0; u < kArmBatch; u++) {
             const int j = u + 1;
-            if (open && j <= lim[e] && !fails(cand[e][u], prev, j)) {
+            const bool far = j > L2;
+            if (open && j <= lim[e] && pass(cand[e][u], far ? K2p : K1p, far ? pK2 : pK1, kq, qk)) {
                 n = j;
-                prev = cand[e][u];
+                kq = k1 - cand[e][u];
+                qk = cand[e][u] + k1;
             } else {
                 open = false;
             }
         }
-        // longer arms: continue one candidate at a time
-        for (int j = kArmBatch + 1; open && j <= lim[e]; j++) {
-            const uint32_t c = __ldg(rgbx + i + j * step[e]);
-            if (fails(c, prev, j)) break;
-            n = j;
-            prev = c;
+        // longer arms: one candidate at a time, up to L2 then beyond
+        if (open) {
+            const uint32_t *q = rgbx + i + (ptrdiff_t)n * step[e];
+            int j = n + 1;
+            for (const int l = min(lim[e], L2); j <= l; j++) {
+                q += step[e];
+                const uint32_t c = __ldg(q);
+                if (!pass(c, K1p, pK1, kq, qk)) { open = false; break; }
+                kq = k1 - c;
+                qk = c + k1;
+            }
+            if (open) {
+                for (; j <= lim[e]; j++) {
+                    q += step[e];
+                    const uint32_t c = __ldg(q);
+                    if (!pass(c, K2p, pK2, kq, qk)) break;
+                    kq = k1 - c;
+                    qk = c + k1;
+                }
+            }
+            n = j - 1;
         }
         arm[e] = n;
     }
