@@ -70,25 +70,36 @@ def peaks():
         return PEAKS_FALLBACK, "fallback"
 
 
+MATCHER_SOURCES = ("dco_stereo.cu", "kernels.cuh")   # the files that define the matcher's kernels
+
+
 def source_digest() -> str:
+    """Digest of the matcher kernels' source files, stamped into the ncu
+    summaries under profiles/ (a summary of other source is not used)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2203_02300_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in MATCHER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_02300_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    that summary was taken on the current kernel source (else None)."""
+def ncu_figure(kernel: str, key: str):
+    """A per-launch figure (`key: value` line) of `kernel` from the committed
+    ncu summary, if that summary was taken on the current kernel source
+    (else None)."""
     dig = source_digest()
     for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md")):
         text = open(path).read()
         m = re.search(r"source_digest:\s*(\w+)", text)
-        t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        t = re.search(key + r":\s*([0-9.eE+]+)", text)
         if m and t and m.group(1) == dig:
             return float(t.group(1))
     return None
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + write.sum)."""
+    return ncu_figure(kernel, "traffic_bytes_per_launch")
 
 
 # ------------------------------------------------------------------- clocks
@@ -269,6 +280,17 @@ def own_arm(args):
             "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
             "traffic": ncu_traffic(dom), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
             if src == "measured" else "fallback 6.8 TB/s"}
+    # the on-chip pipe that binds the dominant kernel: shared-memory data
+    # wavefronts (one 128-byte wavefront per SM per cycle) from the committed
+    # ncu summary, over the live duration, against SMs x the sampled SM clock
+    wf = ncu_figure(dom, "shared_wavefronts_per_launch")
+    if wf and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = wf / (kernels[dom]["avg_us"] * 1e-6) / 1e9
+        pk_wf = sms * clk["sm_mhz"] * 1e-3
+        roof["on_chip"] = {"pipe": "L1 shared-memory data path", "achieved": round(ach, 1), "peak": round(pk_wf, 1),
+                           "unit": "G wavefronts/s", "frac": round(ach / pk_wf, 4),
+                           "wavefronts_per_launch": int(wf), "peak_source": f"{sms} SMs x {clk['sm_mhz']} MHz"}
 
     # ---- cost + aggregation against a staged design: a staged path streams
     # 16 B per view-evaluation (cost write, H read and write, V read); this one
