@@ -255,3 +255,158 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_resid(const DnArgs a)
 }
 
 }  // namespace dco
+
+// ------------------------------------------------------------- C ABI
+// (this header is included by dco_stereo.cu at file scope, after the handle
+// and the launch helpers)
+extern "C" {
+
+dco_status dco_dense_params_default(dco_dense_params *p)
+{
+    if (!p) return DCO_EINVAL;
+    p->lambda_d = 0.80f;    // Sect. 7.2
+    p->lambda_s = 1.20f;
+    p->lambda_s2 = 0.02f;
+    p->tol = 1e-5f;
+    p->max_iters = 4000;
+    return DCO_OK;
+}
+
+dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_t *contour, const float *m_fuse,
+                              const float *m_int, const float *d_pre, int W, int H, const dco_dense_params *pin,
+                              float *d_out, dco_stream stream)
+{
+    if (!h || !d_sparse || !d_out || W < 1 || H < 1 || W > 32768 || H > 32768) return DCO_EINVAL;   // W*H < 2^31
+    dco_dense_params p;
+    if (pin) p = *pin;
+    else dco_dense_params_default(&p);
+    if (!(p.lambda_d >= 0.f) || !(p.lambda_s >= 0.f) || !(p.lambda_s2 >= 0.f) || !(p.tol > 0.f) ||
+        p.max_iters < 0 || p.max_iters > 1000000)
+        return DCO_EINVAL;
+    DCO_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DCO_CUDA(h, cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        h->last_error = "dco_stereo_densify waits for its solve and cannot be captured";
+        return DCO_EINVAL;
+    }
+    const size_t n = (size_t)W * H;
+    // grid-stride kernels: at most 8 resident blocks per multiprocessor
+    int nsm = 0;
+    DCO_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int nblk = (int)std::min<size_t>((n + kDnBlock - 1) / kDnBlock, (size_t)std::max(nsm, 1) * 8);
+    // workspace: r, z, p0, p1, Ap, wr, wd, diag, b; block partials; scalars
+    const size_t fl = align_up(4 * n);
+    const size_t off_part = 9 * fl, off_sc = off_part + align_up(16 * (size_t)nblk);
+    dco_status st = ensure_ws(h, off_sc + align_up(sizeof(DnScalars)));
+    if (st != DCO_OK) return st;
+    if (!h->dn_pin) {
+        DCO_CUDA(h, cudaMallocHost((void **)&h->dn_pin, 2 * sizeof(int)));
+        for (auto &e : h->dn_ev) DCO_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    DnArgs a;
+    std::memset(&a, 0, sizeof a);   // padding included: the bytes key the captured graph
+    a.ds = d_sparse; a.dpre = d_pre; a.mf = m_fuse; a.mi = m_int; a.contour = contour;
+    float *f = ws_ptr<float>(h, 0);
+    auto arr = [&](int k) { return reinterpret_cast<float *>(reinterpret_cast<char *>(f) + k * fl); };
+    a.x = d_out; a.r = arr(0); a.z = arr(1); a.p[0] = arr(2); a.p[1] = arr(3); a.ap = arr(4);
+    a.wr = arr(5); a.wd = arr(6); a.dg = arr(7); a.b = arr(8);
+    a.part = ws_ptr<double>(h, off_part);
+    a.sc = ws_ptr<DnScalars>(h, off_sc);
+    a.W = W; a.H = H; a.nblk = nblk;
+    a.lambda_d = p.lambda_d; a.lambda_s = p.lambda_s; a.lambda_s2 = p.lambda_s2;
+    a.tol2 = (double)p.tol * p.tol;
+    {
+        ProfScope ps(h, s, "k_dn_setup");
+        k_dn_setup<<<nblk, kDnBlock, 0, s>>>(a);
+    }
+    {
+        ProfScope ps(h, s, "k_dn_init");
+        k_dn_init<<<nblk, kDnBlock, 0, s>>>(a);
+    }
+    DCO_CUDA(h, cudaGetLastError());
+    // Iterations run in batches of kDnIters, each closed by the residual
+    // replacement, the true-residual test and a copy of the (sticky) done
+    // flag to pinned memory.  A batch is one CUDA graph launch (captured once
+    // per argument set on a private stream; per-kernel profiling uses plain
+    // launches instead); the host keeps one batch queued ahead and stops
+    // enqueuing once the flag of an earlier batch reads 1.
+    constexpr int kDnIters = 16;   // even: buffer parity repeats per batch
+    auto enqueue = [&](cudaStream_t q, int it0, int m, bool prof) -> cudaError_t {
+        for (int k = 0; k < m; k++) {
+            const int it = it0 + k;
+            {
+                ProfScope ps(h, q, prof ? "k_dn_ap" : nullptr);
+                k_dn_ap<<<nblk, kDnBlock, 0, q>>>(a, it);
+            }
+            {
+                ProfScope ps(h, q, prof ? "k_dn_upd" : nullptr);
+                k_dn_upd<<<nblk, kDnBlock, 0, q>>>(a, it);
+            }
+        }
+        {
+            ProfScope ps(h, q, prof ? "k_dn_resid" : nullptr);
+            k_dn_resid<<<nblk, kDnBlock, 0, q>>>(a);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->dn_pin, &a.sc->done, sizeof(int), cudaMemcpyDeviceToHost, q);
+        return e;
+    };
+    const bool graph = !h->profiling;
+    if (graph) {
+        const unsigned char *ka = reinterpret_cast<const unsigned char *>(&a);
+        if (!h->dn_exec || h->dn_key.size() != sizeof a || std::memcmp(h->dn_key.data(), ka, sizeof a)) {
+            if (h->dn_exec) {
+                cudaGraphExecDestroy(h->dn_exec);
+                h->dn_exec = nullptr;
+            }
+            if (!h->dn_stream) DCO_CUDA(h, cudaStreamCreateWithFlags(&h->dn_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            DCO_CUDA(h, cudaStreamBeginCapture(h->dn_stream, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e = enqueue(h->dn_stream, 0, kDnIters, false);
+            const cudaError_t e2 = cudaStreamEndCapture(h->dn_stream, &g);
+            DCO_CUDA(h, e);
+            DCO_CUDA(h, e2);
+            const cudaError_t e3 = cudaGraphInstantiate(&h->dn_exec, g, 0);
+            cudaGraphDestroy(g);
+            DCO_CUDA(h, e3);
+            h->dn_key.assign(ka, ka + sizeof a);
+        }
+    }
+    *h->dn_pin = 0;
+    int it = 0, nb = 0;
+    bool stop = false;
+    while (it < p.max_iters && !stop) {
+        const int m = std::min(kDnIters, p.max_iters - it);
+        if (graph && m == kDnIters) {
+            DCO_CUDA(h, cudaGraphLaunch(h->dn_exec, s));
+            h->launches += 2 * kDnIters + 1;
+        } else {
+            DCO_CUDA(h, enqueue(s, it, m, true));
+        }
+        it += m;
+        DCO_CUDA(h, cudaEventRecord(h->dn_ev[nb & 1], s));
+        if (nb > 0) {
+            DCO_CUDA(h, cudaEventSynchronize(h->dn_ev[(nb - 1) & 1]));
+            stop = *reinterpret_cast<volatile int *>(h->dn_pin) != 0;
+        }
+        nb++;
+    }
+    DnScalars sc{};
+    DCO_CUDA(h, cudaMemcpyAsync(&sc, a.sc, sizeof sc, cudaMemcpyDeviceToHost, s));
+    DCO_CUDA(h, cudaStreamSynchronize(s));
+    h->dn_iters = sc.iters;
+    h->dn_relres = sc.bb > 0.0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+    return DCO_OK;
+}
+
+dco_status dco_stereo_densify_stats(dco_stereo *h, int *iters, double *rel_residual)
+{
+    if (!h) return DCO_EINVAL;
+    if (iters) *iters = h->dn_iters;
+    if (rel_residual) *rel_residual = h->dn_relres;
+    return DCO_OK;
+}
+
+}  // extern "C"
