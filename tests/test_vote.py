@@ -125,3 +125,20 @@ def test_vote_over_smoothed_arms(env):
     p = binding.Params.default(vote_iters=2, smooth_arms=1)
     got = st.vote(_dev(torch, s.left), _dev(torch, d), 24, p).cpu().numpy()
     assert np.array_equal(got, O.vote(d, O.arms(s.left, O.Params(smooth_arms=1)), 24, 2))
+
+
+@pytest.mark.parametrize("over", [dict(), dict(agg_order=1), dict(smooth_arms=1), dict(agg_order=1, smooth_arms=1)])
+def test_whole_path_with_vote_equals_the_oracle_chain(env, over):
+    # the oracle's own chain, independent of the GPU's intermediate maps:
+    # Eqs. 1-3 (decision in the kernel's precision), the consistency check,
+    # two Eq. 4 rounds over the order-0 regions of the (possibly smoothed)
+    # left arms
+    torch, binding, st = env
+    s = scenes.plane_scene(160, 96, 24, 4, seed=scenes.seed_for(2, 990), slanted=True, noise_sigma=2.0,
+                           drange=(2, 21), texture="mixed")
+    L, R = _dev(torch, s.left), _dev(torch, s.right)
+    got = st.match(L, R, s.D, binding.Params.default(vote_iters=2, **over)).cpu().numpy()
+    op = O.Params(**over)
+    ref = O.match(s.left, s.right, s.D, op, quantized=True)
+    want = O.vote(ref.qdisp, O.arms(s.left, op), s.D, 2)
+    assert np.array_equal(got, want)
