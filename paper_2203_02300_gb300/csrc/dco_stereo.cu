@@ -5,20 +5,22 @@
 // outlier removal by left-right consistency, Sect. 4.3).
 //
 // Pipeline per pair (one stream, no host round trip):
-//   k_prep   grey + census (shared-memory window) + four arms (shared-memory
-//            cross tile) for both images -> 16-byte records + arm words
+//   k_pack   RGB -> packed colour words and the grey level, both images
+//   k_prep   census (shared-memory grey tile) + the four arms (walks over the
+//            packed colours) -> 16-byte records + arm words
 //   per pass of dc disparities:
-//     k_hagg  Eq. 1 cost in fixed point, running row prefix in registers,
-//             a 2*L1+2 deep ring of prefixes per lane in shared memory, and
+//     k_hagg  Eq. 1 cost in fixed point for every (column, disparity) of a
+//             row, prefixes over 16-column segments in shared memory, and
 //             the horizontal segment sum of every pixel -> sh slice
-//     k_vagg  running column prefix of sh, the same ring along y, the
-//             vertical sum over the up/down arms (Eq. 2), WTA (Eq. 3) by a
-//             warp min-reduction, merged with the previous passes
+//     k_vagg  column prefix of the sh slice (TMA tiles), the vertical sum
+//             over the up/down arms (Eq. 2) and the running minimum over
+//             the disparities (Eq. 3), merged with the previous passes
 //   k_lr     left-right consistency -> disparity map
-// Lanes of a warp always hold consecutive disparities of one pixel: the
-// record of the reference pixel is a broadcast load, the 32 candidates are
-// consecutive records, ring accesses hit 32 distinct banks, and the slices
-// are written and read as 128-byte lines.
+// Lanes of a warp hold consecutive disparities of one pixel (pairs of them
+// in k_hagg's cost phase): the reference record is a broadcast load, the
+// candidates are consecutive records, prefix rows hit distinct banks, and
+// the slices are written and read as full 128-byte lines.
+
 #include "kernels.cuh"
 #include "dco_stereo.h"
 
@@ -295,18 +297,22 @@ __device__ __forceinline__ void smooth_body(const SmoothArgs &a, int i, int img)
 
 // ------------------------------------------------------------------ k_hagg
 // Block = one row segment of one reference view for one group of 32
-// disparities (lane = disparity d0 + 32*g + lane).  Stage 0 copies (cp.async)
-// the tables, the reference records of the prefix range [xa, xb) (the
-// output columns plus an L1 reach on both sides), the candidate records of
-// the group and the output columns' arms into shared memory.  Then:
-//   A. each warp walks a segment of kHSegCost columns: Eq. 1 cost rounded to
-//      fixed point, local inclusive prefix into P[x - xa][lane];
-//   B. segment totals -> exclusive offsets, added to P in place;
-//   C. every output column xo: S_H = P(xo + r) - P(xo - l - 1) (the
-//      horizontal part of Eq. 2).
-// Unsigned wrap-around makes the P differences exact segment sums.
+// disparities.  Stage 0 copies (cp.async) the tables, the reference records
+// of the prefix range [xa, xb) (the output columns plus an L1 reach on both
+// sides), the candidate records of the whole group (census and colour apart,
+// even and odd candidate indices apart) and the output columns' arms into
+// shared memory.  Then:
+//   A. each half-warp walks a segment of 16 columns; lane j of the half holds
+//      the disparity pair (dlo + 2j, dlo + 2j + 1): Eq. 1 costs rounded to
+//      fixed point, local inclusive prefixes into P[x - xa][d - dlo].  The
+//      candidate of d + 1 at column x + 1 is the candidate of d at x (the
+//      other way round in the right-reference view), so each column step
+//      loads one new candidate record for two evaluations;
+//   C. every output column xo: S_H = F(xo + r) - F(xo - l - 1) (the
+//      horizontal part of Eq. 2), F the row prefix: the difference of the
+//      local prefixes plus the totals of the segments in between.
+// Unsigned wrap-around makes the differences exact segment sums.
 constexpr int kTabBytes = (kTabAD + kTabCen) * 4;
-constexpr int kHU = 4;
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
@@ -325,44 +331,32 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// byte offsets of the H block's shared-memory regions
+// byte offsets of the H block's shared-memory regions.  Candidate indices
+// run over [0, len + 31); index i sits at position i >> 1 of the even (i & 1
+// = 0) or odd array, hh positions each.
 struct HSmem {
-    int ref, oth, arm, p, t, total;
+    int ref, oth, hh, col, arm, p, t, total;
     __host__ __device__ HSmem(int len, int chunk, int nw)
     {
         ref = kTabBytes;
-        oth = ref + len * 16;
-        arm = oth + (len + 32) * 16;
+        oth = ref + len * 16;                   // census: uint2 [2][hh]
+        hh = (len + 33) / 2;
+        col = oth + hh * 16;                    // colour: uint32 [2][hh]
+        arm = oth + (hh * 24 + 15) / 16 * 16;
         p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
         t = p + len * 128;
-        total = t + nw * 128;
+        total = t + 2 * nw * 128;               // segment totals [2 nw][32]
     }
 };
 
-// Phases B and C of a horizontal pass (cost or vote).  P holds every warp's
-// local inclusive prefix of its segment [sa, sb) (relative to the prefix
-// range), T the segment totals (visible after a barrier).
-//   B. exclusive segment offsets, added to P in place;
-//   C. every output column c (n_out of them, prefix index base + c):
-//      S_H = P(c + r) - P(c - l - 1), written to o + c * ds (the horizontal
-//      part of Eq. 2).  Unsigned wrap-around makes the differences exact.
-__device__ __forceinline__ void hagg_tail(uint32_t *P, const uint32_t *T, const uchar4 *sarm, int sa, int sb,
-                                          int n_out, int base, uint32_t *o, size_t ds)
+// Phase C of a horizontal pass: every output column c (n_out of them, prefix
+// index base + c): S_H = P(c + r) - P(c - l - 1), written to o + c * ds (the
+// horizontal part of Eq. 2).  P holds complete prefixes (after phase B).
+// Unsigned wrap-around makes the differences exact.
+__device__ __forceinline__ void hagg_out(const uint32_t *P, const uchar4 *sarm, int n_out, int base, uint32_t *o,
+                                         size_t ds)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    uint32_t offs = 0;
-    for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
-    if (warp > 0) {
-        uint32_t *q = P + sa * 32 + lane;
-        int x = sa;
-        for (; x + 8 <= sb; x += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; u++) q[u * 32] += offs;
-            q += 256;
-        }
-        for (; x < sb; x++, q += 32) *q += offs;
-    }
-    __syncthreads();
     const size_t ostep = (size_t)nw * ds;
     o += warp * ds;
     const uint32_t *Pl = P + lane;
@@ -383,6 +377,119 @@ __device__ __forceinline__ void hagg_tail(uint32_t *P, const uint32_t *T, const 
     }
 }
 
+// Phase C of k_hagg: every output column c (n_out of them, prefix index
+// base + c): S_H = F(c + r) - F(c - l - 1), F the row prefix of the costs.
+// P holds prefixes local to the 16-column segments of phase A and T the
+// segment totals, so F(hi) - F(lo) = P(hi) - P(lo) + the totals of segments
+// seg(lo) .. seg(hi) - 1 (lo = -1 reads the zero row in segment 0); no pass
+// over P adds offsets.  Each half-warp takes one column, lane j of the half
+// the disparities 2j and 2j + 1 (8-byte loads and stores).
+__device__ __forceinline__ void hagg_out_pairs(const uint32_t *P, const uint32_t *T, const uchar4 *sarm, int n_out,
+                                               int base, uint32_t *o, size_t ds)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int hl = lane & 15;
+    const uint2 *P2 = reinterpret_cast<const uint2 *>(P) + hl;
+    const uint2 *T2 = reinterpret_cast<const uint2 *>(T) + hl;
+    uint2 *o2 = reinterpret_cast<uint2 *>(o) + hl;
+    const size_t ds2 = ds / 2;
+    auto column = [&](int i) -> uint2 {
+        const uchar4 am = sarm[i];
+        const int hi = base + i + am.y, lo = base + i - am.x - 1;   // lo >= -1
+        const uint2 a = P2[hi * 16], b = P2[lo * 16];
+        uint2 v = make_uint2(a.x - b.x, a.y - b.y);
+        for (int s = max(lo, 0) >> 4; s < (hi >> 4); s++) {
+            const uint2 t = T2[s * 16];
+            v.x += t.x;
+            v.y += t.y;
+        }
+        return v;
+    };
+    int i = 2 * warp + (lane >> 4);
+    const int step = 2 * nw;
+    for (; i + step < n_out; i += 2 * step) {
+        const uint2 v0 = column(i), v1 = column(i + step);
+        o2[(size_t)i * ds2] = v0;
+        o2[(size_t)(i + step) * ds2] = v1;
+    }
+    if (i < n_out) o2[(size_t)i * ds2] = column(i);
+}
+
+// Phases B and C of a horizontal pass (cost or vote) whose warps each scanned
+// one segment.  P holds every warp's local inclusive prefix of its segment
+// [sa, sb) (relative to the prefix range), T the segment totals (visible
+// after a barrier).
+//   B. exclusive segment offsets, added to P in place;
+//   C. hagg_out.
+__device__ __forceinline__ void hagg_tail(uint32_t *P, const uint32_t *T, const uchar4 *sarm, int sa, int sb,
+                                          int n_out, int base, uint32_t *o, size_t ds)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t offs = 0;
+    for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
+    if (warp > 0) {
+        uint32_t *q = P + sa * 32 + lane;
+        int x = sa;
+        for (; x + 8 <= sb; x += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) q[u * 32] += offs;
+            q += 256;
+        }
+        for (; x < sb; x++, q += 32) *q += offs;
+    }
+    __syncthreads();
+    hagg_out(P, sarm, n_out, base, o, ds);
+}
+
+// Phase A of k_hagg for one half-warp segment [sa, sb) (relative to xa) of
+// view kView.  Lane j of the half (hl) holds the disparities da = dlo + 2 hl
+// and da + 1, the prefixes run_a, run_b.  The candidate index of the record
+// loaded new at column x is x + nb (odd at even x): view 0 pairs it with da
+// and the previous one with da + 1, view 1 the other way round.  A match
+// outside the image costs 1 (Sint): view 0 needs x >= va / vb, view 1 x < va / vb.
+template <int kView>
+__device__ __forceinline__ void hagg_costs(const uint4 *sref, const uint2 *scen, const uint32_t *scol, int hh,
+                                           const float *sTA, const float *sTC, uint32_t *P, int sa, int sb, int hl,
+                                           int va, int vb, float Sf, uint32_t Sint, uint32_t &run_a,
+                                           uint32_t &run_b)
+{
+    const int nb = kView ? 1 + 2 * hl : 31 - 2 * hl;
+    const int p0 = (sa + nb - 1) >> 1;
+    const uint2 *cE = scen + p0 + 1, *cO = scen + hh + p0;   // new records at odd / even steps
+    const uint32_t *kE = scol + p0 + 1, *kO = scol + hh + p0;
+    uint2 pc = scen[p0];
+    uint32_t pk = scol[p0];
+    uint2 *Pp = reinterpret_cast<uint2 *>(P) + hl;
+    auto cost = [&](const uint4 &pr, float av, float sav, uint2 c, uint32_t col) -> uint32_t {
+        const int h = __popc(pr.x ^ c.x) + __popc(pr.y ^ c.y);
+        const int k = (int)__dp4a(__vabsdiffu4(pr.z, col), 0x00010101u, 0u);
+        return __float2uint_rn(fmaf(av, sTA[k], sav * sTC[h]));
+    };
+    auto step = [&](int x, uint2 nc, uint32_t nk) {
+        const uint4 pr = sref[x];
+        const float av = __uint_as_float(pr.w), sav = Sf - av;
+        const uint32_t qa = kView ? cost(pr, av, sav, pc, pk) : cost(pr, av, sav, nc, nk);
+        const uint32_t qb = kView ? cost(pr, av, sav, nc, nk) : cost(pr, av, sav, pc, pk);
+        run_a += (kView ? x < va : x >= va) ? qa : Sint;
+        run_b += (kView ? x < vb : x >= vb) ? qb : Sint;
+        Pp[x * 16] = make_uint2(run_a, run_b);
+        pc = nc;
+        pk = nk;
+    };
+    if (sb - sa == 16) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            step(sa + 2 * k, cO[k], kO[k]);
+            step(sa + 2 * k + 1, cE[k], kE[k]);
+        }
+    } else {
+        for (int k = 0; sa + 2 * k < sb; k++) {
+            step(sa + 2 * k, cO[k], kO[k]);
+            if (sa + 2 * k + 1 < sb) step(sa + 2 * k + 1, cE[k], kE[k]);
+        }
+    }
+}
+
 __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -396,22 +503,24 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     float *sTA = reinterpret_cast<float *>(smem_raw);
     float *sTC = sTA + kTabAD;
     uint4 *sref = reinterpret_cast<uint4 *>(smem_raw + L.ref);
-    // candidate records, split: census (8 bytes) and colour (4 bytes)
-    uint2 *socen = reinterpret_cast<uint2 *>(smem_raw + L.oth);
-    uint32_t *sorgb = reinterpret_cast<uint32_t *>(smem_raw + L.oth + (len + 32) * 8);
+    uint2 *scen = reinterpret_cast<uint2 *>(smem_raw + L.oth);       // candidate census [2][hh]
+    uint32_t *scol = reinterpret_cast<uint32_t *>(smem_raw + L.col); // candidate colour + Lmin [2][hh]
     uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);
     uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32], P[-1] = 0
-    uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [nw][32]
+    uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [2 nw][32]
     if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
 
     // disparities of this group: [dlo, dhi] live
     const int dlo = a.d0 + 32 * g;
     const int dhi = min(min(a.d0 + a.dc, a.D), dlo + 32) - 1;
-    const int sign = view ? 1 : -1;
-    const int olo = view ? xa + dlo : xa - dhi;                 // candidate range [olo, olo + len + dhi - dlo)
-    const int olen = len + dhi - dlo;
+    // candidate index i <-> column olo + i, i in [0, len + 31): every
+    // disparity of the 32-wide group; the indices of live disparities are
+    // [ilo, ihi), the others are zero-filled (their outputs are never read)
+    const int olo = view ? xa + dlo : xa - dlo - 31;
+    const int olen = len + 31;
+    const int ilo = view ? 0 : 31 - (dhi - dlo), ihi = view ? len + dhi - dlo : olen;
     const uint4 *rref = (view ? a.rec[1] : a.rec[0]) + (size_t)y * a.rpitch;
-    const uint4 *roth = (view ? a.rec[0] : a.rec[1]) + (size_t)y * a.rpitch;   // padded: olo >= -255
+    const uint4 *roth = (view ? a.rec[0] : a.rec[1]) + (size_t)y * a.rpitch;   // padded: live olo + i >= -255
     const uchar4 *aref = (view ? a.arms[1] : a.arms[0]) + (size_t)y * W;
 
     // ---- 0: stage
@@ -419,58 +528,38 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
         cp_async16(smem_raw + 16 * i, reinterpret_cast<const uint8_t *>(a.tables) + 16 * i);
     for (int i = threadIdx.x; i < len; i += blockDim.x) cp_async16(sref + i, rref + xa + i);
     for (int i = threadIdx.x; i < olen; i += blockDim.x) {
-        cp_async8(socen + i, &roth[olo + i].x);   // census words
-        cp_async4(sorgb + i, &roth[olo + i].z);   // colour and Lmin
+        const int pos = (i & 1) * L.hh + (i >> 1);
+        if (i >= ilo && i < ihi) {
+            cp_async8(scen + pos, &roth[olo + i].x);   // census words
+            cp_async4(scol + pos, &roth[olo + i].z);   // colour and Lmin
+        } else {
+            scen[pos] = make_uint2(0u, 0u);
+            scol[pos] = 0u;
+        }
     }
     for (int i = threadIdx.x; i < xe - xs; i += blockDim.x) cp_async4(sarm + i, aref + xs + i);
     cp_async_wait_all();
     __syncthreads();
 
-    const int d = dlo + lane;
-    const bool live = d <= dhi;
-    const int oi = (live ? sign * d : sign * dlo) - olo;   // candidate index = x + oi (in range)
+    // ---- A: costs and local prefixes of this half-warp's segment
+    const int half = lane >> 4, hl = lane & 15;
+    const int s = 2 * warp + half;
+    const int sa = 16 * s, sb = min(len, sa + 16);
+    const int da = dlo + 2 * hl;
     // columns x (relative to xa) whose match x -/+ d lies in the image
-    const int vlo = live ? (view ? 0 : max(0, d - xa)) : 1, vhi = live ? (view ? W - d - xa : len) : 0;
-    const float Sf = a.S;
-    const uint32_t Sint = a.Sint;
-
-    // ---- A: costs and local prefix of this warp's segment
-    const int sa = warp * kHSegCost, sb = min(len, sa + kHSegCost);   // relative to xa
-    uint32_t run = 0;
-    auto cost_at = [&](const uint4 pr, const uint4 po, int x) -> uint32_t {
-        const int h = __popc(pr.x ^ po.x) + __popc(pr.y ^ po.y);
-        const int k = (int)__dp4a(__vabsdiffu4(pr.z, po.z), 0x00010101u, 0u);
-        const float av = __uint_as_float(pr.w);
-        const uint32_t q = __float2uint_rn(fmaf(av, sTA[k], (Sf - av) * sTC[h]));
-        return (unsigned)(x - vlo) < (unsigned)(vhi - vlo) ? q : Sint;   // match outside the image: cost 1
-    };
-    int x0 = sa;
-    for (; x0 + kHU <= sb; x0 += kHU) {
-        uint4 pr[kHU], po[kHU];
-#pragma unroll
-        for (int u = 0; u < kHU; u++) {
-            pr[u] = sref[x0 + u];
-            const uint2 c = socen[x0 + u + xa + oi];
-            po[u] = make_uint4(c.x, c.y, sorgb[x0 + u + xa + oi], 0u);
-        }
-        uint32_t c[kHU];
-#pragma unroll
-        for (int u = 0; u < kHU; u++) c[u] = cost_at(pr[u], po[u], x0 + u);
-#pragma unroll
-        for (int u = 0; u < kHU; u++) {
-            run += c[u];
-            P[(x0 + u) * 32 + lane] = run;
-        }
+    const int va = view ? W - xa - da : da - xa, vb = view ? va - 1 : va + 1;
+    uint32_t run_a = 0, run_b = 0;
+    if (sa < len) {
+        if (view)
+            hagg_costs<1>(sref, scen, scol, L.hh, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
+        else
+            hagg_costs<0>(sref, scen, scol, L.hh, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
     }
-    for (; x0 < sb; x0++) {
-        const uint2 c = socen[x0 + xa + oi];
-        run += cost_at(sref[x0], make_uint4(c.x, c.y, sorgb[x0 + xa + oi], 0u), x0);
-        P[x0 * 32 + lane] = run;
-    }
-    T[warp * 32 + lane] = run;
+    reinterpret_cast<uint2 *>(T + s * 32)[hl] = make_uint2(run_a, run_b);
     __syncthreads();
-    hagg_tail(P, T, sarm, sa, sb, xe - xs, xs - xa,
-              (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32 + lane, a.dstride);
+
+    hagg_out_pairs(P, T, sarm, xe - xs, xs - xa,
+                   (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
 }
 
 // ---------------------------------------------------------------- k_vcost
