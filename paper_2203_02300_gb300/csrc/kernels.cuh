@@ -35,8 +35,9 @@ constexpr int kTabFloats = kTabAD + kTabCen + kTabAlpha;
 // discarded: the cost of a match outside the image is 1).
 constexpr int kRPad = 256;
 
-// The cost H pass scans columns in warp segments of kHSegCost (one chunk per
-// row up to kHMaxLen columns, else 512-column chunks), the vote H pass in
+// The cost H pass gives each warp kHSegCost columns of the prefix range (two
+// half-warp segments of 16; one chunk per row up to kHMaxLen columns, else
+// 512-column chunks), k_vcost each warp kHSegCost rows, the vote H pass
 // segments of kHSeg; the V pass rows in segments of 1 << seglog.
 constexpr int kHSegLog = 6, kHSeg = 1 << kHSegLog;
 constexpr int kHSegCost = 32;
