@@ -308,9 +308,10 @@ __device__ __forceinline__ void smooth_body(const SmoothArgs &a, int i, int img)
 //      candidate of d + 1 at column x + 1 is the candidate of d at x (the
 //      other way round in the right-reference view), so each column step
 //      loads one new candidate record for two evaluations;
+//   B. the exclusive prefix of the segment totals (segment offsets);
 //   C. every output column xo: S_H = F(xo + r) - F(xo - l - 1) (the
 //      horizontal part of Eq. 2), F the row prefix: the difference of the
-//      local prefixes plus the totals of the segments in between.
+//      local prefixes plus the difference of their segments' offsets.
 // Unsigned wrap-around makes the differences exact segment sums.
 constexpr int kTabBytes = (kTabAD + kTabCen) * 4;
 
@@ -339,7 +340,7 @@ struct HSmem {
     __host__ __device__ HSmem(int len, int chunk, int nw)
     {
         ref = kTabBytes;
-        oth = ref + len * 16;                   // census: uint2 [2][hh]
+        oth = ref + len * 16;                   // census: uint2 [2][hh]; then the segment offsets
         hh = (len + 33) / 2;
         col = oth + hh * 16;                    // colour: uint32 [2][hh]
         arm = oth + (hh * 24 + 15) / 16 * 16;
@@ -349,96 +350,68 @@ struct HSmem {
     }
 };
 
-// Phase C of a horizontal pass: every output column c (n_out of them, prefix
-// index base + c): S_H = P(c + r) - P(c - l - 1), written to o + c * ds (the
-// horizontal part of Eq. 2).  P holds complete prefixes (after phase B).
-// Unsigned wrap-around makes the differences exact.
-__device__ __forceinline__ void hagg_out(const uint32_t *P, const uchar4 *sarm, int n_out, int base, uint32_t *o,
-                                         size_t ds)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const size_t ostep = (size_t)nw * ds;
-    o += warp * ds;
-    const uint32_t *Pl = P + lane;
-    int i = warp;
-    for (; i + nw < n_out; i += 2 * nw, o += 2 * ostep) {
-        const uchar4 am0 = sarm[i], am1 = sarm[i + nw];
-        const int hi0 = base + i + am0.y, lo0 = base + i - am0.x - 1;   // lo >= -1
-        const int hi1 = base + i + nw + am1.y, lo1 = base + i + nw - am1.x - 1;
-        const uint32_t v0 = Pl[hi0 * 32] - Pl[lo0 * 32];
-        const uint32_t v1 = Pl[hi1 * 32] - Pl[lo1 * 32];
-        o[0] = v0;
-        o[ostep] = v1;
-    }
-    if (i < n_out) {
-        const uchar4 am = sarm[i];
-        const int hi = base + i + am.y, lo = base + i - am.x - 1;
-        *o = Pl[hi * 32] - Pl[lo * 32];
-    }
-}
-
-// Phase C of k_hagg: every output column c (n_out of them, prefix index
-// base + c): S_H = F(c + r) - F(c - l - 1), F the row prefix of the costs.
-// P holds prefixes local to the 16-column segments of phase A and T the
-// segment totals, so F(hi) - F(lo) = P(hi) - P(lo) + the totals of segments
-// seg(lo) .. seg(hi) - 1 (lo = -1 reads the zero row in segment 0); no pass
-// over P adds offsets.  Each half-warp takes one column, lane j of the half
-// the disparities 2j and 2j + 1 (8-byte loads and stores).
-__device__ __forceinline__ void hagg_out_pairs(const uint32_t *P, const uint32_t *T, const uchar4 *sarm, int n_out,
+// Phase C of a horizontal pass: every output column c (n_out of them,
+// prefix index base + c): S_H = F(c + r) - F(c - l - 1), F the prefix of the
+// costs along the scan.  P holds prefixes local to segments of 1 << kSegLog
+// positions and OFF the exclusive prefix of the segment totals, so
+// F(x) = OFF[x >> kSegLog] + P(x) and F(-1) = 0 (the zero row in front of P,
+// segment 0 whose offset is 0); no pass over P adds offsets.  Each
+// quarter-warp takes one column, lane j of the quarter the disparities
+// 4j .. 4j + 3 of the group (16-byte loads and stores, one 128-byte prefix
+// row per quarter).  Unsigned wrap-around makes the differences exact.
+template <int kSegLog>
+__device__ __forceinline__ void hagg_out_quads(const uint32_t *P, const uint32_t *OFF, const uchar4 *sarm, int n_out,
                                                int base, uint32_t *o, size_t ds)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int hl = lane & 15;
-    const uint2 *P2 = reinterpret_cast<const uint2 *>(P) + hl;
-    const uint2 *T2 = reinterpret_cast<const uint2 *>(T) + hl;
-    uint2 *o2 = reinterpret_cast<uint2 *>(o) + hl;
-    const size_t ds2 = ds / 2;
-    auto column = [&](int i) -> uint2 {
+    const int l8 = lane & 7;
+    const uint4 *P4 = reinterpret_cast<const uint4 *>(P) + l8;
+    const uint4 *F4 = reinterpret_cast<const uint4 *>(OFF) + l8;
+    uint4 *o4 = reinterpret_cast<uint4 *>(o) + l8;
+    const size_t ds4 = ds / 4;
+    auto column = [&](int i) -> uint4 {
         const uchar4 am = sarm[i];
         const int hi = base + i + am.y, lo = base + i - am.x - 1;   // lo >= -1
-        const uint2 a = P2[hi * 16], b = P2[lo * 16];
-        uint2 v = make_uint2(a.x - b.x, a.y - b.y);
-        for (int s = max(lo, 0) >> 4; s < (hi >> 4); s++) {
-            const uint2 t = T2[s * 16];
-            v.x += t.x;
-            v.y += t.y;
+        const uint4 a = P4[hi * 8], b = P4[lo * 8];
+        uint4 v = make_uint4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+        const int sh = hi >> kSegLog, sl = max(lo, 0) >> kSegLog;
+        if (sh != sl) {   // the arm interval crosses segment boundaries
+            const uint4 fh = F4[sh * 8], fl = F4[sl * 8];
+            v.x += fh.x - fl.x;
+            v.y += fh.y - fl.y;
+            v.z += fh.z - fl.z;
+            v.w += fh.w - fl.w;
         }
         return v;
     };
-    int i = 2 * warp + (lane >> 4);
-    const int step = 2 * nw;
+    int i = 4 * warp + (lane >> 3);
+    const int step = 4 * nw;
     for (; i + step < n_out; i += 2 * step) {
-        const uint2 v0 = column(i), v1 = column(i + step);
-        o2[(size_t)i * ds2] = v0;
-        o2[(size_t)(i + step) * ds2] = v1;
+        const uint4 v0 = column(i), v1 = column(i + step);
+        o4[(size_t)i * ds4] = v0;
+        o4[(size_t)(i + step) * ds4] = v1;
     }
-    if (i < n_out) o2[(size_t)i * ds2] = column(i);
+    if (i < n_out) o4[(size_t)i * ds4] = column(i);
 }
 
-// Phases B and C of a horizontal pass (cost or vote) whose warps each scanned
-// one segment.  P holds every warp's local inclusive prefix of its segment
-// [sa, sb) (relative to the prefix range), T the segment totals (visible
-// after a barrier).
-//   B. exclusive segment offsets, added to P in place;
-//   C. hagg_out.
-__device__ __forceinline__ void hagg_tail(uint32_t *P, const uint32_t *T, const uchar4 *sarm, int sa, int sb,
-                                          int n_out, int base, uint32_t *o, size_t ds)
+// Phases B and C of a horizontal pass (k_vcost, k_hvote) whose warps each
+// scanned one segment of 1 << kSegLog positions: P holds every warp's local
+// inclusive prefix of its segment, T the segment totals (visible after a
+// barrier).
+//   B. T is replaced by the exclusive prefix of the totals (segment offsets);
+//   C. hagg_out_quads with those offsets.
+template <int kSegLog>
+__device__ __forceinline__ void hagg_tail(const uint32_t *P, uint32_t *T, const uchar4 *sarm, int n_out, int base,
+                                          uint32_t *o, size_t ds)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t offs = 0;
+#pragma unroll 4
     for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
-    if (warp > 0) {
-        uint32_t *q = P + sa * 32 + lane;
-        int x = sa;
-        for (; x + 8 <= sb; x += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; u++) q[u * 32] += offs;
-            q += 256;
-        }
-        for (; x < sb; x++, q += 32) *q += offs;
-    }
     __syncthreads();
-    hagg_out(P, sarm, n_out, base, o, ds);
+    T[warp * 32 + lane] = offs;
+    __syncthreads();
+    hagg_out_quads<kSegLog>(P, T, sarm, n_out, base, o, ds);
 }
 
 // Phase A of k_hagg for one half-warp segment [sa, sb) (relative to xa) of
@@ -558,8 +531,21 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     reinterpret_cast<uint2 *>(T + s * 32)[hl] = make_uint2(run_a, run_b);
     __syncthreads();
 
-    hagg_out_pairs(P, T, sarm, xe - xs, xs - xa,
-                   (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
+    // ---- B: exclusive offsets of the segments holding columns (lane =
+    // disparity), written over the candidate records, which are no longer read
+    uint32_t *OFF = reinterpret_cast<uint32_t *>(smem_raw + L.oth);   // [ceil(len / 16)][32]
+    if (32 * warp < len) {
+        uint32_t offs = 0;
+#pragma unroll 4
+        for (int s2 = 0; s2 < 2 * warp; s2++) offs += T[s2 * 32 + lane];
+        OFF[2 * warp * 32 + lane] = offs;
+        if (32 * warp + 16 < len) OFF[(2 * warp + 1) * 32 + lane] = offs + T[2 * warp * 32 + lane];
+    }
+    __syncthreads();
+
+    // ---- C
+    hagg_out_quads<4>(P, OFF, sarm, xe - xs, xs - xa,
+                      (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
 }
 
 // ---------------------------------------------------------------- k_vcost
@@ -656,9 +642,9 @@ __device__ __forceinline__ void vcost_body(const HArgs &a, int bx, int by, int b
     T[warp * 32 + lane] = run;
     __syncthreads();
     // consecutive output rows are one slice row (W * dstride words) apart
-    hagg_tail(P, T, sarm, sa, sb, ye - ys, ys - ya,
-              (view ? a.sh[1] : a.sh[0]) + ((size_t)ys * W + x) * a.dstride + g * 32 + lane,
-              (size_t)W * a.dstride);
+    static_assert(kHSegCost == 1 << 5, "k_vcost segments: 32 rows per warp");
+    hagg_tail<5>(P, T, sarm, ye - ys, ys - ya, (view ? a.sh[1] : a.sh[0]) + ((size_t)ys * W + x) * a.dstride + g * 32,
+                 (size_t)W * a.dstride);
 }
 
 // ---------------------------------------------------------------- k_hvote
@@ -709,8 +695,7 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
     }
     T[warp * 32 + lane] = run;
     __syncthreads();
-    hagg_tail(P, T, sarm, sa, sb, xe - xs, xs - xa, a.sh + ((size_t)y * W + xs) * a.dstride + g * 32 + lane,
-              a.dstride);
+    hagg_tail<kHSegLog>(P, T, sarm, xe - xs, xs - xa, a.sh + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
 }
 
 // ------------------------------------------------------------------ k_vagg
