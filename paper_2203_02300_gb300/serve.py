@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import threading
 import time
 from concurrent.futures import Future
@@ -267,13 +268,20 @@ def run_config4(frames_per_stream: int = 300, rate_hz: float = 30.0, time_scale:
     events.sort()
     srv = Server(shapes, device=device, **(server_kw or {}))
     futs = {}
-    t0 = time.perf_counter()
-    for t, i, k in events:
-        now = time.perf_counter() - t0
-        if t > now:
-            time.sleep(t - now)
-        l, r = frames[i][k % unique_frames]
-        futs[(i, k)] = srv.submit(i, l, r, arrival=t0 + t)
-    outs = {key: f.result(timeout=120) for key, f in futs.items()}
+    # a full collection of the Python heap mid-replay pauses every thread of
+    # the serving loop at once: collect before the replay, not during it
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for t, i, k in events:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            l, r = frames[i][k % unique_frames]
+            futs[(i, k)] = srv.submit(i, l, r, arrival=t0 + t)
+        outs = {key: f.result(timeout=120) for key, f in futs.items()}
+    finally:
+        gc.enable()
     srv.close()
     return srv.stats(), outs, frames
