@@ -297,9 +297,14 @@ def own_arm(args):
     # 8 B (H writes the horizontal sums, V reads them)
     evals = 2 * npx * D
     hv_us = sum(kernels[k]["avg_us"] * kernels[k]["launches"] for k in ("k_hagg", "k_vagg") if k in kernels) / args.steps
+    # a staged design (cost slice written, read and rewritten by H, read by
+    # V) moves 16 B per view-evaluation; its HBM-bound time against ours
+    staged_us = 16 * evals / (pk["hbm_gbs"] * 1e3)
     staged = {"ours_h_plus_v_us": round(hv_us, 2), "ours_bytes_per_eval": 8, "staged_bytes_per_eval": 16,
               "ours_bytes_at_hbm_peak_us": round(8 * evals / (pk["hbm_gbs"] * 1e3), 2),
-              "staged_bytes_at_hbm_peak_us": round(16 * evals / (pk["hbm_gbs"] * 1e3), 2)}
+              "staged_bytes_at_hbm_peak_us": round(staged_us, 2),
+              "staged_at_60pct_hbm_us": round(staged_us / 0.6, 2),
+              "staged_roofline_frac_equivalent": round(staged_us / hv_us, 4) if hv_us > 0 else None}
 
     # ---- config 3 (batched) and config 4 (serving), rank 0 only
     extras = {}
