@@ -554,9 +554,10 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
 // chunk of rows) of one reference view for one group of 32 disparities;
 // lane = disparity.  The reference records of the column are staged in
 // shared memory; the candidates of each row (32 neighbouring records of the
-// other view's row) are read straight from the record rows.  Then the phases
-// of k_hagg along the column: warp segments of 32 rows, offsets, segment
-// sums (hagg_tail, with the up / down arms), written to the same slice layout.
+// other view's row) are read straight from the record rows.  Then the
+// phases of a horizontal pass along the column: local prefixes over warp
+// segments of 32 rows, segment offsets, segment sums (hagg_tail, with the
+// up / down arms), written to the same slice layout.
 struct CSmem {
     int ref, arm, p, t, total;
     __host__ __device__ CSmem(int len, int chunk, int nw)
@@ -648,10 +649,12 @@ __device__ __forceinline__ void vcost_body(const HArgs &a, int bx, int by, int b
 }
 
 // ---------------------------------------------------------------- k_hvote
-// Horizontal pass of the parallax optimisation (Sect. 4.3, Eq. 4): the same
-// block layout and phases as k_hagg, with the cost replaced by the indicator
-// [disp(x, y) == d] of the map being voted on (-1 matches no d), so S_H holds
-// the number of pixels of each horizontal segment that vote for d.
+// Horizontal pass of the parallax optimisation (Sect. 4.3, Eq. 4): block =
+// (row, group of 32 disparities), lane = disparity, local prefixes over warp
+// segments of 64 columns of the indicator [disp(x, y) == d] of the map being
+// voted on (-1 matches no d), then the output phase of the horizontal passes
+// (hagg_tail), so S_H holds the number of pixels of each horizontal segment
+// that vote for d.
 struct HVSmem {
     int disp, arm, p, t, total;
     __host__ __device__ HVSmem(int len, int chunk, int nw)
