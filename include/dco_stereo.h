@@ -30,6 +30,9 @@
  *     Limits: 1 <= W, H <= 16384; 1 <= D <= 256; D <= W; 1 <= arm_l1 <= 40;
  *     census window odd, at most 64 bits; lambda_ad, lambda_census, eps > 0;
  *     gamma_l >= 0.
+ *   - A workspace the device cannot allocate returns DCO_ENOMEM (one beyond
+ *     the handle's budget DCO_EBUDGET) before anything is enqueued; the
+ *     handle stays usable, and its next calls allocate what they need.
  *   - Device-side failures do not trap: they set the handle's status word,
  *     read with dco_stereo_sync_status() (DCO_EDEVICE).  The vertical pass
  *     sets bit 0 when a TMA tile copy does not complete within its bounded

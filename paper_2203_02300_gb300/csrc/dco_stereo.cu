@@ -1322,10 +1322,24 @@ struct dco_stereo {
 
 namespace {
 
+// A failed runtime call also leaves its error as the thread's last error;
+// it is reported here and then dropped, so that the launch checks of the
+// next call (cudaGetLastError after a launch) see only their own launches.
 dco_status cuda_fail(dco_stereo *h, cudaError_t e, const char *what)
 {
     if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? DCO_ENOMEM : DCO_ECUDA;
+}
+
+// Entry of a call that launches work: h's device made current, and a
+// non-sticky error that an earlier runtime call left in this thread dropped
+// (it belongs to that call, not to this one's launches).
+cudaError_t enter_device(const dco_stereo *h)
+{
+    const cudaError_t e = cudaSetDevice(h->device);
+    (void)cudaGetLastError();
+    return e;
 }
 
 #define DCO_CUDA(h, call)                                              \
@@ -1887,7 +1901,7 @@ dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
         h->last_error = "invalid parameters";
         return DCO_EINVAL;
     }
-    DCO_CUDA(h, cudaSetDevice(h->device));
+    DCO_CUDA(h, enter_device(h));
     return DCO_OK;
 }
 
@@ -2158,7 +2172,7 @@ dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *dis
 dco_status dco_stereo_downscale(dco_stereo *h, const uint8_t *rgb, int W, int H, uint8_t *out, dco_stream stream)
 {
     if (!h || !rgb || !out || W < 2 || H < 2 || W > 2 * 16384 || H > 2 * 16384) return DCO_EINVAL;
-    DCO_CUDA(h, cudaSetDevice(h->device));
+    DCO_CUDA(h, enter_device(h));
     cudaStream_t s = (cudaStream_t)stream;
     DownArgs da{};
     da.src[0] = rgb; da.dst[0] = out; da.W = W; da.H = H;
@@ -2226,7 +2240,7 @@ dco_status dco_stereo_lr_check(dco_stereo *h, const int16_t *dl, const int16_t *
                                int16_t *out, dco_stream stream)
 {
     if (!h || !dl || !dr || !out || W < 1 || H < 1) return DCO_EINVAL;
-    DCO_CUDA(h, cudaSetDevice(h->device));
+    DCO_CUDA(h, enter_device(h));
     std::vector<Item<LrArgs>> it(1);
     it[0].a.dl = dl; it[0].a.dr = dr; it[0].a.out = out;
     it[0].a.W = W; it[0].a.H = H; it[0].a.tol = tol;
@@ -2258,7 +2272,7 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
 dco_status dco_stereo_sync_status(dco_stereo *h)
 {
     if (!h) return DCO_EINVAL;
-    DCO_CUDA(h, cudaSetDevice(h->device));
+    DCO_CUDA(h, enter_device(h));
     DCO_CUDA(h, cudaDeviceSynchronize());
     int v = 0;
     DCO_CUDA(h, cudaMemcpy(&v, h->d_status, sizeof v, cudaMemcpyDeviceToHost));
@@ -2360,6 +2374,7 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     if (tab_bytes + status_bytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DCO_ECUDA;
+    (void)cudaGetLastError();   // an earlier call's error is not this call's launch failure
     void *base = nullptr;
     dco_status st = noalloc_base(dev, &base);
     if (st != DCO_OK) return st;

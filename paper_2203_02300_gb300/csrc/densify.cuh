@@ -283,7 +283,7 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
     if (!(p.lambda_d >= 0.f) || !(p.lambda_s >= 0.f) || !(p.lambda_s2 >= 0.f) || !(p.tol > 0.f) ||
         p.max_iters < 0 || p.max_iters > 1000000)
         return DCO_EINVAL;
-    DCO_CUDA(h, cudaSetDevice(h->device));
+    DCO_CUDA(h, enter_device(h));
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     DCO_CUDA(h, cudaStreamIsCapturing(s, &cap));
