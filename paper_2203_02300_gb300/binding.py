@@ -151,9 +151,42 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+def _is_np(t) -> bool:
+    return isinstance(t, np.ndarray)
+
+
+def _contiguous(t) -> bool:
+    return t.flags.c_contiguous if _is_np(t) else t.is_contiguous()
+
+
+def _dtype_ok(t, name: str) -> bool:
+    """t's element type is `name` ("uint8", "int16", "float32", "int64")."""
+    if _is_np(t):
+        return t.dtype == np.dtype(name)
+    import torch
+    return t.dtype == getattr(torch, name)
+
+
+def _expect(what: str, t, shape, dtype: str, like=None) -> None:
+    """Raise ValueError unless `t` is a contiguous (H, W, ...) buffer of the
+    given shape and element type, on the same device as `like` (a torch
+    tensor) when given.  The library trusts the sizes it is passed, so a
+    buffer of the wrong size would be read or written out of bounds."""
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not _dtype_ok(t, dtype):
+        raise ValueError(f"{what}: element type {t.dtype}, expected {dtype}")
+    if not _contiguous(t):
+        raise ValueError(f"{what}: must be contiguous")
+    if like is not None and not _is_np(t) and t.device != like.device:
+        raise ValueError(f"{what}: on {t.device}, expected {like.device}")
+
+
 def _rgb_dims(t) -> tuple[int, int]:
-    assert tuple(t.shape[2:]) == (3,), "images are (H, W, 3) uint8"
-    assert t.is_contiguous(), "images must be contiguous"
+    """(W, H) of an (H, W, 3) uint8 contiguous image (array or tensor)."""
+    if len(t.shape) != 3 or int(t.shape[2]) != 3:
+        raise ValueError(f"images are (H, W, 3) uint8, got shape {tuple(t.shape)}")
+    _expect("image", t, t.shape, "uint8")
     return int(t.shape[1]), int(t.shape[0])
 
 
@@ -194,8 +227,10 @@ class Stereo:
     def match(self, left, right, D: int, params: Optional[Params] = None, out=None, stream=None):
         import torch
         W, H = _rgb_dims(left)
+        _expect("right", right, left.shape, "uint8", left)
         if out is None:
             out = torch.empty((H, W), dtype=torch.int16, device=left.device)
+        _expect("out", out, (H, W), "int16", left)
         _check(lib().dco_stereo_match(self._h, _ptr(left), _ptr(right), W, H, D,
                                       ctypes.byref(params) if params else None, _ptr(out),
                                       _stream(stream)), self._h)
@@ -205,6 +240,7 @@ class Stereo:
                     costs: bool = True):
         import torch
         W, H = _rgb_dims(left)
+        _expect("right", right, left.shape, "uint8", left)
         dev = left.device
         out = torch.empty((H, W), dtype=torch.int16, device=dev)
         dl = torch.empty_like(out)
@@ -219,10 +255,11 @@ class Stereo:
 
     def match_host(self, left: np.ndarray, right: np.ndarray, D: int,
                    params: Optional[Params] = None, out: Optional[np.ndarray] = None, stream=None):
-        H, W, _ = left.shape
-        assert left.flags.c_contiguous and right.flags.c_contiguous
+        W, H = _rgb_dims(left)
+        _expect("right", right, left.shape, "uint8")
         if out is None:
             out = np.empty((H, W), np.int16)
+        _expect("out", out, (H, W), "int16")
         _check(lib().dco_stereo_match_host(self._h, _ptr(left), _ptr(right), W, H, D,
                                            ctypes.byref(params) if params else None, _ptr(out),
                                            _stream(stream)), self._h)
@@ -233,6 +270,8 @@ class Stereo:
         arr = (PairDesc * len(pairs))()
         for i, (l, r, D, o) in enumerate(pairs):
             W, H = _rgb_dims(l)
+            _expect(f"pair {i} right", r, l.shape, "uint8", l)
+            _expect(f"pair {i} out", o, (H, W), "int16", l)
             arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o))
         _check(lib().dco_stereo_match_batch(self._h, arr, len(pairs),
                                             ctypes.byref(params) if params else None, _stream(stream)),
@@ -258,6 +297,7 @@ class Stereo:
     def cost_volume(self, left, right, D: int, view: int, params: Optional[Params] = None, stream=None):
         import torch
         W, H = _rgb_dims(left)
+        _expect("right", right, left.shape, "uint8", left)
         out = torch.empty((D, H, W), dtype=torch.float32, device=left.device)
         _check(lib().dco_stereo_cost_volume(self._h, _ptr(left), _ptr(right), W, H, D,
                                             ctypes.byref(params) if params else None, view, _ptr(out),
@@ -266,7 +306,11 @@ class Stereo:
 
     def lr_check(self, dl, dr, tol: int = 1, stream=None):
         import torch
+        if len(dl.shape) != 2:
+            raise ValueError(f"dl: an (H, W) int16 map, got shape {tuple(dl.shape)}")
         H, W = dl.shape
+        _expect("dl", dl, (H, W), "int16")
+        _expect("dr", dr, (H, W), "int16", dl)
         out = torch.empty_like(dl)
         _check(lib().dco_stereo_lr_check(self._h, _ptr(dl), _ptr(dr), W, H, tol, _ptr(out),
                                          _stream(stream)), self._h)
@@ -277,9 +321,10 @@ class Stereo:
         int16 map `disp` over the support regions of `img` (device tensors)."""
         import torch
         W, H = _rgb_dims(img)
-        assert tuple(disp.shape) == (H, W) and disp.dtype == torch.int16
+        _expect("disp", disp, (H, W), "int16", img)
         if out is None:
             out = torch.empty_like(disp)
+        _expect("out", out, (H, W), "int16", img)
         _check(lib().dco_stereo_vote(self._h, _ptr(img), _ptr(disp), W, H, D,
                                      ctypes.byref(params) if params else None, _ptr(out), _stream(stream)),
                self._h)
@@ -290,9 +335,17 @@ class Stereo:
         """Dense depth (Sect. 6, Eq. 20) from device float maps (H, W); returns
         the output tensor (the call waits for the solve)."""
         import torch
+        if len(d_sparse.shape) != 2:
+            raise ValueError(f"d_sparse: an (H, W) float32 map, got shape {tuple(d_sparse.shape)}")
         H, W = d_sparse.shape
+        _expect("d_sparse", d_sparse, (H, W), "float32")
+        for what, t, dt in (("contour", contour, "uint8"), ("m_fuse", m_fuse, "float32"),
+                            ("m_int", m_int, "float32"), ("d_pre", d_pre, "float32")):
+            if t is not None:
+                _expect(what, t, (H, W), dt, d_sparse)
         if out is None:
             out = torch.empty((H, W), dtype=torch.float32, device=d_sparse.device)
+        _expect("out", out, (H, W), "float32", d_sparse)
         opt = lambda t: _ptr(t) if t is not None else None
         _check(lib().dco_stereo_densify(self._h, _ptr(d_sparse), opt(contour), opt(m_fuse), opt(m_int),
                                         opt(d_pre), W, H, ctypes.byref(params) if params else None, _ptr(out),
@@ -317,8 +370,12 @@ class Stereo:
         matched at half of each axis over D disparities."""
         import torch
         W, H = _rgb_dims(left)
+        _expect("right", right, left.shape, "uint8", left)
         if out is None:
             out = torch.empty((H, W), dtype=torch.float32, device=left.device)
+        _expect("out", out, (H, W), "float32", left)
+        if disp_half is not None:
+            _expect("disp_half", disp_half, (H // 2, W // 2), "int16", left)
         _check(lib().dco_stereo_depth(self._h, _ptr(left), _ptr(right), W, H, D,
                                       ctypes.byref(params) if params else None, float(f_px), float(baseline),
                                       _ptr(out), _ptr(disp_half) if disp_half is not None else None,
