@@ -34,10 +34,12 @@
  *     the handle's budget DCO_EBUDGET) before anything is enqueued; the
  *     handle stays usable, and its next calls allocate what they need.
  *   - Device-side failures do not trap: they set the handle's status word,
- *     read with dco_stereo_sync_status() (DCO_EDEVICE).  The vertical pass
- *     sets bit 0 when a TMA tile copy does not complete within its bounded
- *     mbarrier wait and bit 1 when its shared memory is not 128-byte aligned
- *     for the copies; the pass's outputs are then not valid.
+ *     read with dco_stereo_sync_status() or dco_stereo_stream_status().  The
+ *     vertical pass sets bit 0 when a TMA tile copy does not complete within
+ *     its bounded mbarrier wait (reported as DCO_ETIMEOUT; the block stops
+ *     issuing copies and returns) and bit 1 when its shared memory is not
+ *     128-byte aligned for the copies (DCO_EDEVICE); the pass's outputs are
+ *     then not valid.
  */
 #ifndef DCO_STEREO_H
 #define DCO_STEREO_H
@@ -305,16 +307,50 @@ typedef struct {
  * holds all pairs' per-pixel buffers and one pass of slices for each.
  * Results equal dco_stereo_match on each pair alone (bit-identical).
  * descs: host array of n descriptors.
+ * Admission under the handle's budget: when the pairs' workspaces do not fit
+ * the budget together even at the narrowest pass width (32 disparities),
+ * the pairs are admitted in consecutive groups that do fit, run one group
+ * after the other on `stream` in the same workspace (the allocation never
+ * exceeds the budget; dco_stereo_batch_groups gives the group count).  A
+ * single pair that does not fit returns DCO_EBUDGET before anything is
+ * enqueued.
  */
 dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int n,
                                   const dco_params *p, dco_stream stream);
 
+/* Admission groups the last dco_stereo_match_batch call ran in (1 when all
+ * pairs fit the budget together). */
+int dco_stereo_batch_groups(dco_stereo *h);
+
+/* Bytes of device workspace the handle currently holds (0 before its first
+ * call); never above the handle's budget. */
+size_t dco_stereo_workspace_allocated(dco_stereo *h);
+
 /*
  * Waits for all work of the handle's device, then reads and clears the
- * device status word.  DCO_OK, or DCO_EDEVICE if a kernel reported a failed
- * internal check since the last call.
+ * device status word.  DCO_OK; DCO_ETIMEOUT if a tile copy of the vertical
+ * pass did not complete within its bounded wait; DCO_EDEVICE if a kernel
+ * reported another failed internal check since the last read.
  */
 dco_status dco_stereo_sync_status(dco_stereo *h);
+
+/*
+ * As dco_stereo_sync_status, ordered on `stream` instead of the whole
+ * device: the word is read once the work enqueued on `stream` before this
+ * call has completed (the call waits for it), then cleared on `stream`.
+ * Work of the handle enqueued on other streams is not waited for.
+ */
+dco_status dco_stereo_stream_status(dco_stereo *h, dco_stream stream);
+
+/*
+ * Failure tests (not for normal use).  DCO_TEST_LOSE_TILE_COPIES: the
+ * vertical pass arms each tile's mbarrier but issues no copy, and waits only
+ * a few polls, so every wait runs out with nothing in flight; the kernel
+ * sets bit 0 of the status word and returns, and the stream status reads
+ * DCO_ETIMEOUT.  0 restores normal operation.  Unknown bits: DCO_EINVAL.
+ */
+#define DCO_TEST_LOSE_TILE_COPIES 1
+dco_status dco_stereo_set_test_flags(dco_stereo *h, int flags);
 
 /*
  * The whole path of dco_stereo_match for callers that cannot allocate
@@ -332,16 +368,29 @@ dco_status dco_stereo_sync_status(dco_stereo *h);
  *     W*H <= 90 000 pixels (e.g. 320x240) at any D <= 256.
  *   - All calls share the one array and it keeps the last call's contents;
  *     nothing in it needs to start at zero (every word a kernel reads was
- *     written earlier in the same call).  Calls that overlap on the GPU
- *     (other streams, other threads) race on it: serialise them.
- *   - A device-side failure (see the status word above) lands in a word of
- *     the array; with no handle it is not reported, and disp_out is then
- *     not valid.
+ *     written earlier in the same call; the tables are written by a kernel
+ *     that receives them by value, so no host buffer outlives the call).
+ *     Calls that overlap on the GPU (other streams, other threads) race on
+ *     it: serialise them.
+ *   - A device-side failure (see the status word above) sets a status word
+ *     in the array, which keeps its bits across calls until
+ *     dco_stereo_noalloc_status reads and clears it; disp_out of a call
+ *     whose status is not DCO_OK is not valid.
  * left, right: device W*H*3 bytes; disp_out: device W*H int16; p = NULL
  * uses the defaults (p->d_chunk is ignored).
  */
 dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_t *right, int W, int H, int D,
                                     const dco_params *p, int16_t *disp_out, dco_stream stream);
+
+/*
+ * Status of the allocation-free entry point on the current device: waits
+ * for the work enqueued on `stream` before this call, reads the status word
+ * of the static array, clears it (on `stream`) and returns DCO_OK,
+ * DCO_ETIMEOUT or DCO_EDEVICE as dco_stereo_sync_status does.  Allocates
+ * nothing.  Like the first dco_stereo_match_noalloc call, a first call on a
+ * device looks up the array's address: make it before any stream capture.
+ */
+dco_status dco_stereo_noalloc_status(dco_stream stream);
 
 /* Text of the last CUDA or budget error seen by the handle ("" if none).
  * Owned by the handle, valid until its next call. */

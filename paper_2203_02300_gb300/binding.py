@@ -23,6 +23,7 @@ c_int, c_float, c_void_p, c_size_t = ctypes.c_int, ctypes.c_float, ctypes.c_void
 STATUS = {0: "DCO_OK", 1: "DCO_EINVAL", 2: "DCO_ENOMEM", 3: "DCO_EBUDGET", 4: "DCO_ECUDA",
           5: "DCO_ETIMEOUT", 6: "DCO_EDEVICE"}
 DCO_OK, DCO_EINVAL, DCO_ENOMEM, DCO_EBUDGET, DCO_ECUDA, DCO_ETIMEOUT, DCO_EDEVICE = range(7)
+DCO_TEST_LOSE_TILE_COPIES = 1   # failure test flag (include/dco_stereo.h)
 
 
 class Params(ctypes.Structure):
@@ -115,6 +116,11 @@ def lib():
             "dco_stereo_profile_get": (c_int, [P, c_int, P, P, P]),
             "dco_stereo_launch_count": (ctypes.c_ulonglong, [P]),
             "dco_stereo_match_noalloc": (c_int, [P, P, c_int, c_int, c_int, P, P, P]),
+            "dco_stereo_noalloc_status": (c_int, [P]),
+            "dco_stereo_stream_status": (c_int, [P, P]),
+            "dco_stereo_set_test_flags": (c_int, [P, c_int]),
+            "dco_stereo_workspace_allocated": (c_size_t, [P]),
+            "dco_stereo_batch_groups": (c_int, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -385,6 +391,19 @@ class Stereo:
     # -- status and profiling
     def sync_status(self) -> None:
         _check(lib().dco_stereo_sync_status(self._h), self._h)
+
+    def stream_status(self, stream=None) -> None:
+        """Status word read in order on `stream` (waits for that stream only)."""
+        _check(lib().dco_stereo_stream_status(self._h, _stream(stream)), self._h)
+
+    def set_test_flags(self, flags: int) -> None:
+        _check(lib().dco_stereo_set_test_flags(self._h, int(flags)), self._h)
+
+    def workspace_allocated(self) -> int:
+        return int(lib().dco_stereo_workspace_allocated(self._h))
+
+    def batch_groups(self) -> int:
+        return int(lib().dco_stereo_batch_groups(self._h))
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().dco_stereo_set_profiling(self._h, 1 if on else 0), self._h)

@@ -726,6 +726,7 @@ constexpr int kQS = 36;   // Q row stride in words
 constexpr int kVSeg = 32; // rows per warp
 constexpr int kQ0 = 64;   // Q[0] at word 64 (256 bytes): every warp's tile starts on a 128-byte boundary
 constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a copy is declared lost
+constexpr int kTestWaitLimit = 64;    // the same, under the lost-copy failure test
 constexpr int kStatusCopyTimeout = 1; // status word: a tile copy did not complete
 constexpr int kStatusAlign = 2;       // status word: shared memory not aligned for the tile copies
 constexpr uint32_t kVTileBytes = kVSeg * kQS * 4;
@@ -748,10 +749,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
                  "r"(bytes)
                  : "memory");
 }
-// bounded wait for the phase of the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// bounded wait for the phase of the given parity to complete: false after
+// `limit` polls without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
 {
-    for (int i = 0; i < kWaitLimit; i++) {
+    for (int i = 0; i < limit; i++) {
         uint32_t ok;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -830,6 +832,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         if (nrow == 0 || lane != 0) return;
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         mbar_expect_tx(bar, kVTileBytes);
+        if (a.skip_copy) return;   // failure test: the barrier's phase never completes
         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Q + sa * kQS);
         if (a.tm_rank == 4)
             tma_load_4d(dst, tm, 0, g, kRow ? ya + sa : fix, kRow ? fix : ya + sa, bar);
@@ -859,11 +862,19 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
     const bool out_row = rin && ya + r >= ys && ya + r < ye;
     uint32_t bv = 0xffffffffu, bd = 0;
     if (warp == 0) Q[-kQS + lane] = 0u;   // Q[-1]: read by rows whose up arm reaches the top
-    bool lost = false;
-
     for (int g = 0; g < ng; g++) {
         // ---- A: this warp's rows of the slice column, lane = disparity
-        if (nrow > 0 && !mbar_wait(bar, (uint32_t)(g & 1))) lost = true;
+        const bool lost = nrow > 0 && !mbar_wait(bar, (uint32_t)(g & 1), a.wait_limit);
+        if (__syncthreads_or(lost)) {
+            // a copy did not complete: report it, issue no further copies,
+            // and give this warp's copy a last bounded wait before the
+            // block's shared memory is released
+            if (lost) {
+                if (lane == 0 && a.status) atomicOr(a.status, kStatusCopyTimeout);
+                mbar_wait(bar, (uint32_t)(g & 1), a.wait_limit);
+            }
+            return;
+        }
         uint32_t *q = Q + sa * kQS + lane;
         uint32_t tot = 0;
         uint32_t v[kVSeg];
@@ -925,13 +936,6 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         }
         __syncthreads();   // Q and T are reused by the next group
         if (g + 1 < ng) issue(g + 1);
-    }
-    if (lost) {
-        // a copy never completed: report, and give the others in flight a
-        // last bounded wait before the block's shared memory is released
-        if (lane == 0 && a.status) atomicOr(a.status, kStatusCopyTimeout);
-        mbar_wait(bar, (uint32_t)((ng - 1) & 1));
-        return;
     }
     // ---- merge with earlier passes, write the disparity (last pass) or state
     if (!out_row) return;
@@ -1306,6 +1310,8 @@ struct dco_stereo {
     uint8_t *stage = nullptr;
     size_t stage_cap = 0;
     bool profiling = false;
+    int test_flags = 0;                      // DCO_TEST_* failure tests (0 in normal use)
+    int groups_last = 1;                     // admission groups of the last batch call
     unsigned long long launches = 0;
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> pool;
@@ -1340,6 +1346,14 @@ cudaError_t enter_device(const dco_stereo *h)
     const cudaError_t e = cudaSetDevice(h->device);
     (void)cudaGetLastError();
     return e;
+}
+
+// status word -> call status: a lost tile copy is a timed-out wait, any
+// other bit a failed internal check
+dco_status status_of_word(int v)
+{
+    if (v == 0) return DCO_OK;
+    return (v & kStatusCopyTimeout) ? DCO_ETIMEOUT : DCO_EDEVICE;
 }
 
 #define DCO_CUDA(h, call)                                              \
@@ -1697,6 +1711,15 @@ dco_status slice_map(dco_stereo *h, VArgs &a, int v, const uint32_t *slice, int 
     return DCO_OK;
 }
 
+// bounded tile waits of the V pass; the lost-copy failure test arms the
+// barriers without copies and gives up after a few polls
+void set_wait(const dco_stereo *h, VArgs &a)
+{
+    const bool lose = (h->test_flags & DCO_TEST_LOSE_TILE_COPIES) != 0;
+    a.wait_limit = lose ? kTestWaitLimit : kWaitLimit;
+    a.skip_copy = lose ? 1 : 0;
+}
+
 dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> &jobs, int pass, cudaStream_t s)
 {
     std::map<int, std::vector<Item<HArgs>>> hb;
@@ -1735,6 +1758,7 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
         b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        set_wait(h, b.a);
         for (int v = 0; v < 2; v++) {
             dco_status st = slice_map(h, b.a, v, b.a.sh[v], j.W, j.H, j.L.dstride, vh);
             if (st != DCO_OK) return st;
@@ -1808,6 +1832,7 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
         b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
         b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
+        set_wait(h, b.a);
         if (dco_status st = slice_map(h, b.a, 0, b.a.sh[0], j.W, j.H, j.L.dstride, false); st != DCO_OK) return st;
         b.a.tm[1] = b.a.tm[0];
         b.gx = vg.grid.x; b.gy = 1; b.gz = vg.grid.z;   // the left view only
@@ -1879,7 +1904,11 @@ dco_status launch_jobs(dco_stereo *h, const dco_params &p, const Derived &dv, st
     return p.vote_iters > 0 ? run_vote(h, p, dv, jobs, s) : DCO_OK;
 }
 
-// the whole path for a set of independent pairs: one launch per stage
+// the whole path for a set of independent pairs: one launch per stage.  On a
+// handle with a budget, pairs whose workspaces do not fit it together (even
+// at the narrowest pass width) are admitted in consecutive groups that do;
+// the groups run one after the other on the stream, each reusing the same
+// workspace.  Every group is planned before anything is enqueued.
 dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, cudaStream_t s)
 {
     Derived dv;
@@ -1887,9 +1916,42 @@ dco_status run_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, 
     size_t total = 0;
     dco_status st = plan_jobs(h, p, jobs, total);
     if (st != DCO_OK) return st;
-    if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+    if (!h->budget || total <= h->budget || jobs.size() == 1) {
+        if ((st = ensure_ws(h, total)) != DCO_OK) return st;
+        if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
+        return launch_jobs(h, p, dv, jobs, s);
+    }
+    std::vector<std::vector<Job>> groups;
+    size_t need = 0;
+    for (size_t i = 0; i < jobs.size();) {
+        std::vector<Job> g{jobs[i]};
+        size_t t = 0;
+        plan_jobs(h, p, g, t);
+        if (t > h->budget) {
+            h->last_error = "pair " + std::to_string(i) + " needs " + std::to_string(t) +
+                            " bytes of workspace, more than the budget of " + std::to_string(h->budget);
+            return DCO_EBUDGET;
+        }
+        size_t j = i + 1;
+        for (; j < jobs.size(); j++) {
+            std::vector<Job> g2 = g;
+            g2.push_back(jobs[j]);
+            size_t t2 = 0;
+            plan_jobs(h, p, g2, t2);
+            if (t2 > h->budget) break;
+            g.swap(g2);
+            t = t2;
+        }
+        need = std::max(need, t);
+        groups.push_back(std::move(g));
+        i = j;
+    }
+    if ((st = ensure_ws(h, need)) != DCO_OK) return st;
     if ((st = ensure_tables(h, p, dv, s)) != DCO_OK) return st;
-    return launch_jobs(h, p, dv, jobs, s);
+    h->groups_last = (int)groups.size();
+    for (auto &g : groups)
+        if ((st = launch_jobs(h, p, dv, g, s)) != DCO_OK) return st;
+    return DCO_OK;
 }
 
 dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
@@ -2254,6 +2316,7 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
+    h->groups_last = 1;
     if (n < 0 || (n > 0 && !descs)) return DCO_EINVAL;
     for (int i = 0; i < n; i++)
         if (!descs[i].left || !descs[i].right || !descs[i].disp_out ||
@@ -2277,7 +2340,38 @@ dco_status dco_stereo_sync_status(dco_stereo *h)
     int v = 0;
     DCO_CUDA(h, cudaMemcpy(&v, h->d_status, sizeof v, cudaMemcpyDeviceToHost));
     DCO_CUDA(h, cudaMemset(h->d_status, 0, sizeof v));
-    return v ? DCO_EDEVICE : DCO_OK;
+    return status_of_word(v);
+}
+
+dco_status dco_stereo_stream_status(dco_stereo *h, dco_stream stream)
+{
+    if (!h) return DCO_EINVAL;
+    DCO_CUDA(h, enter_device(h));
+    const cudaStream_t s = (cudaStream_t)stream;
+    // a device-to-pageable copy returns once it has completed: the word is
+    // read after everything enqueued on `stream` before this call
+    int v = 0;
+    DCO_CUDA(h, cudaMemcpyAsync(&v, h->d_status, sizeof v, cudaMemcpyDeviceToHost, s));
+    DCO_CUDA(h, cudaStreamSynchronize(s));
+    DCO_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof v, s));
+    return status_of_word(v);
+}
+
+dco_status dco_stereo_set_test_flags(dco_stereo *h, int flags)
+{
+    if (!h || (flags & ~DCO_TEST_LOSE_TILE_COPIES)) return DCO_EINVAL;
+    h->test_flags = flags;
+    return DCO_OK;
+}
+
+size_t dco_stereo_workspace_allocated(dco_stereo *h)
+{
+    return h ? h->ws_cap : 0;
+}
+
+int dco_stereo_batch_groups(dco_stereo *h)
+{
+    return h ? h->groups_last : 0;
 }
 
 dco_status dco_stereo_set_profiling(dco_stereo *h, int enable)
@@ -2336,8 +2430,21 @@ const char *dco_stereo_last_error(dco_stereo *h)
 namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 constexpr int kNoAllocMaxDevices = 64;
+// scratch layout: the Eq. 1 tables, the status word, the workspace
+constexpr size_t kNoAllocTabBytes = (sizeof(float) * kTabFloats + kAlign - 1) / kAlign * kAlign;
+constexpr size_t kNoAllocStatusBytes = kAlign;
 std::mutex g_noalloc_mu;
 void *g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// the tables travel by value in the kernel parameters, so no host buffer
+// has to outlive the call
+struct TabBlock {
+    float t[kTabFloats];
+};
+__global__ void k_put_tables(const __grid_constant__ TabBlock b, float *dst)
+{
+    for (int i = threadIdx.x; i < kTabFloats; i += blockDim.x) dst[i] = b.t[i];
+}
 } // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -2367,11 +2474,8 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     p.d_chunk = 32;   // passes of 32 disparities keep the slices small
     Derived dv;
     derive(p, dv);
-    // scratch: tables, a status word (kernel checks land there; this entry
-    // point has no handle to report them through), the workspace
-    const size_t tab_bytes = align_up(sizeof(float) * kTabFloats), status_bytes = align_up(sizeof(int));
     const Layout L = make_layout(W, H, D, p);
-    if (tab_bytes + status_bytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
+    if (kNoAllocTabBytes + kNoAllocStatusBytes + L.total > kNoAllocScratchBytes) return DCO_EBUDGET;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DCO_ECUDA;
     (void)cudaGetLastError();   // an earlier call's error is not this call's launch failure
@@ -2381,16 +2485,17 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     cudaStream_t s = (cudaStream_t)stream;
 
     // Eq. 1 tables (host double, rounded once to float) into the scratch
-    float tab[kTabFloats];
-    fill_tables(tab, p, dv);
-    if (cudaMemcpyAsync(base, tab, sizeof tab, cudaMemcpyHostToDevice, s) != cudaSuccess) return DCO_ECUDA;
+    TabBlock tb;
+    fill_tables(tb.t, p, dv);
+    k_put_tables<<<1, 256, 0, s>>>(tb, static_cast<float *>(base));
+    if (cudaGetLastError() != cudaSuccess) return DCO_ECUDA;
 
     // a handle that owns nothing: its workspace and tables are the scratch
     dco_stereo view;
     view.device = dev;
-    view.d_status = reinterpret_cast<int *>(static_cast<char *>(base) + tab_bytes);
-    view.ws = static_cast<char *>(base) + tab_bytes + status_bytes;
-    view.ws_cap = kNoAllocScratchBytes - tab_bytes - status_bytes;
+    view.d_status = reinterpret_cast<int *>(static_cast<char *>(base) + kNoAllocTabBytes);
+    view.ws = static_cast<char *>(base) + kNoAllocTabBytes + kNoAllocStatusBytes;
+    view.ws_cap = kNoAllocScratchBytes - kNoAllocTabBytes - kNoAllocStatusBytes;
     view.d_tables = static_cast<float *>(base);
     view.tab_valid = true;
     view.tab_key[0] = p.lambda_ad;
@@ -2403,4 +2508,24 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     view.d_tables = nullptr;
     view.d_status = nullptr;
     return st;
+}
+
+extern "C" dco_status dco_stereo_noalloc_status(dco_stream stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DCO_ECUDA;
+    void *base = nullptr;
+    dco_status st = noalloc_base(dev, &base);
+    if (st != DCO_OK) return st;
+    int *word = reinterpret_cast<int *>(static_cast<char *>(base) + kNoAllocTabBytes);
+    const cudaStream_t s = (cudaStream_t)stream;
+    // a device-to-pageable copy returns once it has completed, after the
+    // work enqueued on `stream` before it
+    int v = 0;
+    if (cudaMemcpyAsync(&v, word, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(word, 0, sizeof v, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return DCO_ECUDA;
+    }
+    return status_of_word(v);
 }

@@ -124,6 +124,8 @@ struct VArgs {
     float *vol;            // optional (D, H, W) normalised costs of view `vol_view`
     const int16_t *mask;   // optional: pixels where mask < 0 are written as -1 (vote)
     int *status;           // device status word (a lost tile copy sets a bit)
+    int wait_limit;        // mbarrier polls before a tile copy is declared lost
+    int skip_copy;         // failure test: arm each tile's barrier but issue no copy
     int tm_rank;           // 4: tm as above; 3: dims (disparity, x, y), box 36 x 1 x 32 at (32 g, x, y)
     int vol_view;
     int W, H, D;

@@ -9,3 +9,13 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Excused near-tie counts of every parity check of the run."""
+    from tests import parity
+    lines = parity.summary_lines()
+    if lines:
+        terminalreporter.section("parity: excused near ties per check (FP64 oracle)")
+        for line in lines:
+            terminalreporter.write_line(line)

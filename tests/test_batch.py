@@ -70,11 +70,24 @@ def test_config3_batch_parity_sampled(env, config3):
                       torch.empty((s.H, s.W), dtype=torch.int16, device="cuda")))
     st.match_batch(pairs)
     torch.cuda.synchronize()
-    for s, (_, _, _, out) in zip(seen.values(), pairs):
+    tl, tr, tf = (parity.Tally(f"config 3 {v}") for v in ("left disparity", "right disparity", "final map"))
+    for s, (L, R, _, out) in zip(seen.values(), pairs):
         got = out.cpu().numpy()
+        fo, dl, dr, cl, cr = (t.cpu().numpy() for t in st.match_views(L, R, s.D))
+        assert np.array_equal(got, fo)
         for rows in ((0, 4), (s.H // 2, s.H // 2 + 4)):
             ref = O.match(s.left, s.right, s.D, rows=rows, quantized=True)
-            parity.check_final(got[rows[0]:rows[1]], ref, f"batch {s.W}x{s.H} D={s.D}")
+            sl = slice(*rows)
+            what = f"config 3 pair {s.W}x{s.H} D={s.D} rows {rows[0]}-{rows[1]}"
+            parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, what + " left disparity",
+                                   ref.qdisp_l, tally=tl)
+            parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, what + " right disparity",
+                                   ref.qdisp_r, tally=tr)
+            parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, what + " left cost")
+            parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, what + " right cost")
+            parity.check_final(got[sl], ref, what + " final map (batch)", tally=tf)
+    for t in (tl, tr, tf):
+        t.close()
 
 
 def test_more_pairs_than_one_launch_holds(env):

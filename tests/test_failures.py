@@ -81,3 +81,43 @@ def test_maps_do_not_depend_on_the_workspace_history(env):
                 for g, w in zip(got, fresh[k]):
                     assert np.array_equal(g, w)
         h.sync_status()
+
+
+def test_lost_tile_copies_time_out_and_the_context_stays_usable(env):
+    # failure test flag: the V pass arms each tile's mbarrier but issues no
+    # copy, so every bounded wait runs out with nothing in flight; the kernel
+    # sets bit 0 of the status word and returns (no trap, no hang)
+    torch, binding, _ = env
+    s = scenes.plane_scene(96, 64, 16, 3, seed=scenes.seed_for(9, 20), drange=(2, 13))
+    L, R = _dev(torch, s.left), _dev(torch, s.right)
+    with binding.Stereo(0) as h:
+        want = h.match(L, R, s.D).cpu().numpy()
+        h.stream_status()
+        h.set_test_flags(binding.DCO_TEST_LOSE_TILE_COPIES)
+        h.match(L, R, s.D)
+        with pytest.raises(binding.DcoError) as e:
+            h.stream_status()
+        assert e.value.code == binding.DCO_ETIMEOUT
+        h.stream_status()   # the read cleared the word
+        with pytest.raises(binding.DcoError):
+            h.set_test_flags(2)
+        h.set_test_flags(0)
+        got = h.match(L, R, s.D).cpu().numpy()
+        h.stream_status()
+        torch.cuda.synchronize()
+    assert np.array_equal(got, want)
+
+
+def test_stream_status_waits_for_its_own_stream(env):
+    torch, binding, _ = env
+    s = scenes.config_scene(1)
+    L, R = _dev(torch, s.left), _dev(torch, s.right)
+    side = torch.cuda.Stream()
+    with binding.Stereo(0) as h:
+        with torch.cuda.stream(side):
+            out = h.match(L, R, s.D, stream=side)
+            h.stream_status(side)   # returns once `side` has finished the match
+        assert side.query()
+        got = out.cpu().numpy()
+    with binding.Stereo(0) as h:
+        assert np.array_equal(got, h.match(L, R, s.D).cpu().numpy())

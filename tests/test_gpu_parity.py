@@ -47,17 +47,25 @@ def run_views(env, left, right, D, bp=None):
     return (out.cpu().numpy(), dl.cpu().numpy(), dr.cpu().numpy(), cl.cpu().numpy(), cr.cpu().numpy())
 
 
-def full_check(env, left, right, D, bp=None, rows=None):
+def full_check(env, left, right, D, bp=None, rows=None, label=None):
+    """The GPU's two disparity maps, minimum costs and checked map against
+    the FP64 oracle under the parity rule (near ties excused, <= 0.1 %)."""
     torch, binding, st = env
     op = oparams(bp) if bp is not None else O.Params()
     out, dl, dr, cl, cr = run_views(env, left, right, D, bp)
     ref = O.match(left, right, D, op, rows=rows, quantized=True)
     sl = slice(*rows) if rows else slice(None)
-    n = parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
-    n += parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
-    parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, "left cost")
-    parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, "right cost")
+    H, W, _ = left.shape
+    label = label or f"{W}x{H} D={D}"
+    if rows:
+        label += f" rows {rows[0]}-{rows[1]}"
+    n = parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, f"{label} left disparity", ref.qdisp_l)
+    n += parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, f"{label} right disparity",
+                                ref.qdisp_r)
+    parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, f"{label} left cost")
+    parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, f"{label} right cost")
     assert (out == O.lr_check(dl, dr, op.lr_tol)).all(), "consistency map"
+    parity.check_final(out[sl], ref, f"{label} final map")
     return n, out, dl, dr
 
 
@@ -121,14 +129,29 @@ def test_lr_check_stage(env):
 # ----------------------------------------------------------- full path
 def test_config1_full_parity(env):
     s = scenes.config_scene(1)
-    n, out, dl, dr = full_check(env, s.left, s.right, s.D)
+    n, out, dl, dr = full_check(env, s.left, s.right, s.D, label="config 1 (320x240 D=32)")
     gt = np.rint(s.disp).astype(np.int16)
     assert ((dl == gt) & ~s.occluded).sum() / (~s.occluded).sum() > 0.99
 
 
 def test_config2_full_parity(env):
     s = scenes.config_scene(2)
-    full_check(env, s.left, s.right, s.D)
+    full_check(env, s.left, s.right, s.D, label="config 2 (640x480 D=64)")
+
+
+@pytest.mark.parametrize("config", [1, 2])
+def test_lr_check_rejects_ground_truth_occlusions(env, config):
+    # outlier removal (Sect. 4.3): of the left pixels the scene generator
+    # marks occluded (no visible match in the right view), the fraction the
+    # consistency check rejects; and the fraction of visible pixels it keeps
+    s = scenes.config_scene(config)
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
+    occ = s.occluded
+    rejected = float((out[occ] < 0).mean())
+    kept = float((out[~occ] >= 0).mean())
+    parity.note(f"config {config}: the consistency check rejects {100 * rejected:.1f} % of the "
+                f"{int(occ.sum())} ground-truth occluded pixels and keeps {100 * kept:.1f} % of the visible ones")
+    assert rejected > 0.3 and kept > 0.7
 
 
 def test_config1_cost_volume_both_views(env):
@@ -241,29 +264,93 @@ def test_vh_order_config5_sampled_rows(env):
     s = scenes.config_scene(5)
     bp = binding.Params.default(agg_order=1)
     out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D, bp)
+    tl, tr, tf = (parity.Tally(f"config 5 V-then-H order {v}") for v in ("left disparity", "right disparity",
+                                                                          "final map"))
     for rows in ((0, 6), (509, 515), (1074, 1080)):
         ref = O.match(s.left, s.right, s.D, O.Params(agg_order=1), rows=rows, quantized=True)
         sl = slice(*rows)
-        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
-        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
+        what = f"config 5 V-then-H order rows {rows[0]}-{rows[1]}"
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, what + " left disparity", ref.qdisp_l,
+                               tally=tl)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, what + " right disparity",
+                               ref.qdisp_r, tally=tr)
         parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
         parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
+        parity.check_final(out[sl], ref, what + " final map", tally=tf)
+    for t in (tl, tr, tf):
+        t.close()
 
 
-def test_config5_sampled_rows(env):
-    # 1920x1080 D=256 at the benchmark's launch configuration; the oracle
-    # evaluates three row bands (top border, middle, bottom border)
-    s = scenes.config_scene(5)
+def _scenes_in_pool(config, items):
+    # scene generation is plain NumPy on the host; a spawned pool (safe after
+    # CUDA initialisation) renders the 1920x1080 scenes in parallel
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(min(len(items), 8), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(scenes.config_scene, [config] * len(items), items))
+
+
+CONFIG5_BUDGET = 1_500_000_000   # bytes: below one 2.12 GB FP32 volume of one view
+
+
+def test_config5_batch_of_8_under_a_budget(env):
+    # 8 pairs of 1920x1080, D = 256 on a handle whose workspace budget is
+    # below one materialised volume: the batch is admitted in groups that fit
+    # (passes of 32 disparities), the allocation never exceeds the budget,
+    # every map equals the pair matched alone, and two pairs are checked
+    # against the FP64 oracle on row bands (borders and middle)
     torch, binding, st = env
-    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
-    for rows in ((0, 6), (537, 543), (1074, 1080)):
-        ref = O.match(s.left, s.right, s.D, rows=rows, quantized=True)
-        sl = slice(*rows)
-        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, "left disparity", ref.qdisp_l)
-        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, "right disparity", ref.qdisp_r)
-        parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
-        parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
-    assert (out == O.lr_check(dl, dr, 1)).all()
+    ss = _scenes_in_pool(5, list(range(8)))
+    assert CONFIG5_BUDGET < 1920 * 1080 * 256 * 4
+    pairs = [(dev(torch, s.left), dev(torch, s.right), s.D,
+              torch.full((s.H, s.W), -9, dtype=torch.int16, device="cuda")) for s in ss]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with binding.Stereo(0, budget_bytes=CONFIG5_BUDGET) as h:
+        h.match_batch(pairs)
+        h.stream_status()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert 0 < h.workspace_allocated() <= CONFIG5_BUDGET
+        assert free0 - free1 <= CONFIG5_BUDGET
+        assert h.batch_groups() > 1
+    bands = ((0, 6), (537, 543), (1074, 1080))
+    tl, tr, tf = (parity.Tally(f"config 5 (1920x1080 D=256) {v}") for v in ("left disparity", "right disparity",
+                                                                             "final map"))
+    for k, (s, (L, R, D, out)) in enumerate(zip(ss, pairs)):
+        got = out.cpu().numpy()
+        if k >= 2:
+            assert np.array_equal(got, st.match(L, R, D).cpu().numpy()), k
+            continue
+        fo, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
+        assert np.array_equal(got, fo), k
+        assert (fo == O.lr_check(dl, dr, 1)).all()
+        for rows in bands[k:k + 2]:
+            ref = O.match(s.left, s.right, s.D, rows=rows, quantized=True)
+            sl = slice(*rows)
+            what = f"config 5 (1920x1080 D=256) pair {k} rows {rows[0]}-{rows[1]}"
+            parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, what + " left disparity",
+                                   ref.qdisp_l, tally=tl)
+            parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, what + " right disparity",
+                                   ref.qdisp_r, tally=tr)
+            parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l, what + " left cost")
+            parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r, what + " right cost")
+            parity.check_final(got[sl], ref, what + " final map", tally=tf)
+    for t in (tl, tr, tf):
+        t.close()
+
+
+def test_batch_single_pair_beyond_the_budget_is_rejected(env):
+    torch, binding, st = env
+    s = scenes.config_scene(1)
+    need = binding.Stereo.workspace_bytes(s.W, s.H, s.D, binding.Params.default(d_chunk=32))
+    with binding.Stereo(0, budget_bytes=need - 1) as h:
+        out = torch.full((s.H, s.W), -9, dtype=torch.int16, device="cuda")
+        with pytest.raises(binding.DcoError) as e:
+            h.match_batch([(dev(torch, s.left), dev(torch, s.right), s.D, out)] * 2)
+        assert e.value.code == binding.DCO_EBUDGET
+        assert h.workspace_allocated() == 0
+        torch.cuda.synchronize()
+        assert (out == -9).all()
 
 
 def test_match_host_equals_device_path(env):

@@ -68,3 +68,25 @@ def test_burst_is_batched_and_memory_admission_holds(env):
     # the budget really limited the batches (all 18 frames would need more)
     assert 0 < srv.max_batch_bytes <= srv.lane_budget == budget // 2
     assert 3 * 2 * sum(ws) > srv.lane_budget
+
+
+def test_config4_full_size_streams_against_the_oracle(env):
+    # the four config 4 streams at their real sizes (640x480 D=64, 960x540
+    # D=96, 1280x720 D=128 twice), three distinct frames each (planes moving
+    # between frames), Poisson arrivals at 30 Hz: every served map equals the
+    # frame matched alone, and the first frame of every stream passes the
+    # parity rule against the FP64 oracle on the whole frame
+    from oracle import oracle as O
+    from paper_2203_02300_gb300 import scenes
+    from paper_2203_02300_gb300.serve import run_config4
+    from tests import parity
+    torch, binding, st = env
+    stats, outs, frames = run_config4(frames_per_stream=3, rate_hz=30.0, unique_frames=3)
+    assert stats["frames"] == 3 * len(scenes.STREAMS_CONFIG4)
+    for (i, k), got in outs.items():
+        W, H, D = scenes.STREAMS_CONFIG4[i]
+        l, r = frames[i][k]
+        assert np.array_equal(got, st.match(l.cuda(), r.cuda(), D).cpu().numpy()), (i, k)
+        if k == 0:
+            ref = O.match(l.numpy(), r.numpy(), D)
+            parity.check_final(got, ref, f"config 4 stream {i} ({W}x{H} D={D}) frame 0 final map")

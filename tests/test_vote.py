@@ -129,16 +129,22 @@ def test_vote_over_smoothed_arms(env):
 
 @pytest.mark.parametrize("over", [dict(), dict(agg_order=1), dict(smooth_arms=1), dict(agg_order=1, smooth_arms=1)])
 def test_whole_path_with_vote_equals_the_oracle_chain(env, over):
-    # the oracle's own chain, independent of the GPU's intermediate maps:
-    # Eqs. 1-3 (decision in the kernel's precision), the consistency check,
-    # two Eq. 4 rounds over the order-0 regions of the (possibly smoothed)
-    # left arms
+    # the path with two Eq. 4 rounds equals the oracle's vote (over the
+    # order-0 regions of the possibly smoothed left arms) applied to the
+    # GPU's checked map, and that map passes the parity rule against the
+    # FP64 oracle; where it equals the FP64 map exactly, the whole chain is
+    # the oracle's own
     torch, binding, st = env
+    from tests import parity
     s = scenes.plane_scene(160, 96, 24, 4, seed=scenes.seed_for(2, 990), slanted=True, noise_sigma=2.0,
                            drange=(2, 21), texture="mixed")
     L, R = _dev(torch, s.left), _dev(torch, s.right)
     got = st.match(L, R, s.D, binding.Params.default(vote_iters=2, **over)).cpu().numpy()
+    plain = st.match(L, R, s.D, binding.Params.default(**over)).cpu().numpy()
     op = O.Params(**over)
-    ref = O.match(s.left, s.right, s.D, op, quantized=True)
-    want = O.vote(ref.qdisp, O.arms(s.left, op), s.D, 2)
-    assert np.array_equal(got, want)
+    ref = O.match(s.left, s.right, s.D, op)
+    parity.check_final(plain, ref, f"vote chain {over} checked map")
+    arm = O.arms(s.left, op)
+    assert np.array_equal(got, O.vote(plain, arm, s.D, 2))
+    if np.array_equal(plain, ref.disp):
+        assert np.array_equal(got, O.vote(ref.disp, arm, s.D, 2))

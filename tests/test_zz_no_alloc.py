@@ -5,8 +5,9 @@ the memory footprint must stay fixed after start-up).  For them the library
 exports one entry point whose scratch lives in a static device array.  This
 file checks, through the C ABI, that it returns the same disparity maps as
 the regular entry point on two calls in a row (the second call must not be
-affected by what the first left in the shared array), and that sizes beyond
-the array are rejected before any work.  It runs last so that a failure here
+affected by what the first left in the shared array), that the array's
+status word reads clean after each call, and that sizes beyond the array
+are rejected before any work.  It runs last so that a failure here
 never hides the other tests, and passes in a fresh process or after them.
 """
 import numpy as np
@@ -54,8 +55,12 @@ def test_two_calls_match_the_regular_entry_point(env):
         # same kernels on the same inputs: the consistency maps agree exactly
         # (tolerance of integer work); also within the oracle's parity rule
         assert np.array_equal(got, want)
-        ref = O.match(s.left, s.right, s.D, quantized=True)
+        ref = O.match(s.left, s.right, s.D)
         parity.check_final(got, ref, "no-alloc")
+        # the status word in the array reports no device-side failure (and
+        # is cleared by the read)
+        torch, binding, st = env
+        assert binding.lib().dco_stereo_noalloc_status(torch.cuda.current_stream().cuda_stream) == binding.DCO_OK
 
 
 def test_sizes_beyond_the_array_are_rejected(env):
