@@ -52,7 +52,12 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--d-chunk", type=int, default=0, help="fixed pass width instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 3 batch and config 4 serving runs")
+    ap.add_argument("--extras", default="all",
+                    help="comma list of the extra measurements to run (vote_config2, depth_1280x720, "
+                         "smooth_config2, vh_order_config2, densify_1280x720, batch_config3, batch_config5, "
+                         "serve_config4), or all")
     return ap.parse_args()
 
 
@@ -203,7 +208,7 @@ def own_arm(args):
     R = Rh.to(dev)
     out = torch.empty((H, W), dtype=torch.int16, device=dev)
     st = binding.Stereo(local_rank)
-    dchunk = 0 if args.no_tune else tune.tune_d_chunk(st, L, R, D)
+    dchunk = args.d_chunk if args.d_chunk > 0 else 0 if args.no_tune else tune.tune_d_chunk(st, L, R, D)
     p = binding.Params.default(d_chunk=dchunk)
     npass = -(-D // (dchunk or D))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -292,31 +297,42 @@ def own_arm(args):
                            "unit": "G wavefronts/s", "frac": round(ach / pk_wf, 4),
                            "wavefronts_per_launch": int(wf), "peak_source": f"{sms} SMs x {clk['sm_mhz']} MHz"}
 
-    # ---- cost + aggregation against a staged design: a staged path streams
-    # 16 B per view-evaluation (cost write, H read and write, V read); this one
-    # 8 B (H writes the horizontal sums, V reads them)
-    evals = 2 * npx * D
-    hv_us = sum(kernels[k]["avg_us"] * kernels[k]["launches"] for k in ("k_hagg", "k_vagg") if k in kernels) / args.steps
-    # a staged design (cost slice written, read and rewritten by H, read by
-    # V) moves 16 B per view-evaluation; its HBM-bound time against ours
-    staged_us = 16 * evals / (pk["hbm_gbs"] * 1e3)
-    staged = {"ours_h_plus_v_us": round(hv_us, 2), "ours_bytes_per_eval": 8, "staged_bytes_per_eval": 16,
-              "ours_bytes_at_hbm_peak_us": round(8 * evals / (pk["hbm_gbs"] * 1e3), 2),
-              "staged_bytes_at_hbm_peak_us": round(staged_us, 2),
-              "staged_at_60pct_hbm_us": round(staged_us / 0.6, 2),
-              "staged_roofline_frac_equivalent": round(staged_us / hv_us, 4) if hv_us > 0 else None}
+    # ---- the cost + aggregation kernels together (Eq. 1-3: k_hagg, k_vagg):
+    # their algorithmic bytes over their summed time, against the same peak
+    hv = [k for k in ("k_hagg", "k_vagg") if k in kernels]
+    hv_us = sum(kernels[k]["avg_us"] * kernels[k]["launches"] for k in hv) / args.steps
+    hv_bytes = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in hv) / args.steps
+    costagg = {"kernels": hv, "us_per_frame": round(hv_us, 2), "alg_bytes_per_frame": hv_bytes,
+               "achieved_gbs": round(hv_bytes / (hv_us * 1e-6) / 1e9, 1) if hv_us > 0 else None,
+               "frac_hbm": round(hv_bytes / (hv_us * 1e-6) / 1e9 / pk["hbm_gbs"], 4) if hv_us > 0 else None}
 
     # ---- config 3 (batched) and config 4 (serving), rank 0 only
     extras = {}
-    if rank == 0 and not args.no_extras:
-        extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
-        extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
-        extras["smooth_config2"] = smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
-        extras["vh_order_config2"] = vh_order_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
-        extras["densify_1280x720"] = densify_full_size(torch, binding, st, flush, dev)
-        extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
-        extras["serve_config4"] = serve_config4(torch, binding, st, local_rank)
-        extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0)
+    want = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
+    on = (lambda name: "all" in want or name in want)
+    if rank == 0:
+        if on("vote_config2"):
+            extras["vote_config2"] = vote_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        if on("depth_1280x720"):
+            extras["depth_1280x720"] = depth_full_size(torch, binding, st, flush, dev)
+        if on("smooth_config2"):
+            extras["smooth_config2"] = smooth_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        if on("vh_order_config2"):
+            extras["vh_order_config2"] = vh_order_config2(torch, binding, st, L, R, D, dchunk, flush, dev)
+        if on("densify_1280x720"):
+            extras["densify_1280x720"] = densify_full_size(torch, binding, st, flush, dev)
+        if on("batch_config3"):
+            extras["batch_config3"] = batch_config3(torch, binding, st, flush, dev)
+        if on("batch_config5"):
+            extras["batch_config5"] = batch_config5(torch, binding, flush, dev)
+        if on("serve_config4"):
+            from paper_2203_02300_gb300.serve import render_frames
+            frames4 = render_frames(scenes.STREAMS_CONFIG4, 16, processes=4)
+            d4 = tune.tune_batch(st, scenes.STREAMS_CONFIG4, device=local_rank)
+            extras["serve_config4"] = serve_config4(torch, binding, st, local_rank, frames=frames4, d_chunks=d4)
+            extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0,
+                                                            frames=frames4, d_chunks=d4)
+            extras["serve_config4_saturation"] = serve_saturation(torch, local_rank, frames4, d4)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -338,7 +354,7 @@ def own_arm(args):
                     "latency_ms": {"p50": statistics.median(e2e_ms),
                                    "p99": sorted(e2e_ms)[min(len(e2e_ms) - 1, int(0.99 * len(e2e_ms)))]}},
             "roofline": roof,
-            "cost_aggregation_vs_staged": staged,
+            "cost_aggregation": costagg,
             "kernels": kernels,
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
@@ -593,77 +609,128 @@ def depth_full_size(torch, binding, st, flush, dev, W: int = 1280, H: int = 720,
 
 
 # ------------------------------------------------- config 3 and config 4
+def _timed(torch, dev, flush, fn, reps):
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for _ in range(reps + 2):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms[2:])
+
+
 def batch_config3(torch, binding, st, flush, dev, reps: int = 10):
     """32 pairs of uneven size: one batched pass (CUDA-graph replay) against
-    the same pairs matched one call at a time; L2 flushed before each."""
-    from paper_2203_02300_gb300 import scenes
+    the same pairs matched one call at a time, both with the library's
+    automatic pass width and with each shape's pass width from the autotuner;
+    L2 flushed before each."""
+    from paper_2203_02300_gb300 import scenes, tune
     from paper_2203_02300_gb300.batch import BatchGraph
     sc = scenes.batch_config3(32)
+    shapes = [(s.W, s.H, s.D) for s in sc]
     L = [torch.from_numpy(s.left).to(dev) for s in sc]
     R = [torch.from_numpy(s.right).to(dev) for s in sc]
     outs = [torch.empty((s.H, s.W), dtype=torch.int16, device=dev) for s in sc]
     units = sum(s.W * s.H * s.D for s in sc)
-    g = BatchGraph(binding.Stereo(dev.index or 0), [(s.W, s.H, s.D) for s in sc], device=dev.index or 0)
+    tuned = tune.tune_batch(st, shapes, device=dev.index or 0)
+    g = BatchGraph(binding.Stereo(dev.index or 0), shapes, device=dev.index or 0)
+    gt = BatchGraph(binding.Stereo(dev.index or 0), shapes, device=dev.index or 0, d_chunks=tuned)
     g.load(L, R)
-    stream = torch.cuda.current_stream(dev)
-
-    def timed(fn):
-        ms = []
-        for _ in range(reps + 2):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize(dev)
-            ms.append(a.elapsed_time(b))
-        return statistics.median(ms[2:])
+    gt.load(L, R)
+    pt = [binding.Params.default(d_chunk=dc) for dc in tuned]
 
     def sequential():
         for l, r, s, o in zip(L, R, sc, outs):
             st.match(l, r, s.D, None, o)
 
-    def batched():
-        g.replay()   # launched on the current stream, ordered after the flush
+    def sequential_tuned():
+        for l, r, s, o, p in zip(L, R, sc, outs, pt):
+            st.match(l, r, s.D, p, o)
 
-    t_seq = timed(sequential)
-    t_bat = timed(batched)
-    same = all(torch.equal(a, b) for a, b in zip(outs, g.out))
-    sizes = sorted({(s.W, s.H, s.D) for s in sc})
+    t_seq = _timed(torch, dev, flush, sequential, reps)
+    t_bat = _timed(torch, dev, flush, g.replay, reps)
+    t_seq_t = _timed(torch, dev, flush, sequential_tuned, reps)
+    t_bat_t = _timed(torch, dev, flush, gt.replay, reps)
+    same = all(torch.equal(a, b) and torch.equal(a, c) for a, b, c in zip(outs, g.out, gt.out))
+    sizes = sorted(set(shapes))
+    tiles = {f"{w}x{h} D={d}": tuned[shapes.index((w, h, d))] for w, h, d in sizes}
     return {"pairs": len(sc), "sizes": [f"{w}x{h} D={d}" for w, h, d in sizes], "evals": units,
             "batched_graph_ms": t_bat, "batched_evals_per_s": units / (t_bat * 1e-3),
             "sequential_ms": t_seq, "sequential_evals_per_s": units / (t_seq * 1e-3),
-            "speedup": t_seq / t_bat, "identical_to_sequential": bool(same)}
+            "speedup": t_seq / t_bat,
+            "tuned_pass_width": tiles,
+            "tuned_batched_graph_ms": t_bat_t, "tuned_batched_evals_per_s": units / (t_bat_t * 1e-3),
+            "tuned_sequential_ms": t_seq_t, "tuned_sequential_evals_per_s": units / (t_seq_t * 1e-3),
+            "tuned_batch_over_default_sequential": t_seq / t_bat_t,
+            "identical_to_sequential": bool(same)}
 
 
-def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0):
-    """4 camera streams, 300 frames each, Poisson arrivals at 30 Hz (real
+def batch_config5(torch, binding, flush, dev, reps: int = 3, budget: int = 1_500_000_000):
+    """8 pairs of 1920x1080, D = 256 in one batched call on a handle whose
+    workspace budget is below one 2.12 GB FP32 volume: the library admits the
+    pairs in groups that fit (passes of 32 disparities), the allocation
+    never exceeds the budget.  Scenes rendered in a spawned process pool."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from paper_2203_02300_gb300 import scenes
+    with ProcessPoolExecutor(8, mp_context=mp.get_context("spawn")) as ex:
+        sc = list(ex.map(scenes.config_scene, [5] * 8, range(8)))
+    pairs = [(torch.from_numpy(s.left).to(dev), torch.from_numpy(s.right).to(dev), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device=dev)) for s in sc]
+    units = sum(s.W * s.H * s.D for s in sc)
+    with binding.Stereo(dev.index or 0, budget_bytes=budget) as h:
+        t = _timed(torch, dev, flush, lambda: h.match_batch(pairs), reps)
+        h.stream_status()
+        alloc, groups = h.workspace_allocated(), h.batch_groups()
+    return {"pairs": 8, "size": "1920x1080 D=256", "evals": units, "budget_bytes": budget,
+            "one_volume_bytes": 1920 * 1080 * 256 * 4, "workspace_allocated_bytes": alloc,
+            "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3)}
+
+
+def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, d_chunks=None):
+    """4 camera streams, 300 frames each (cycled from 16 rendered ones per
+    stream, planes moving 0-3 px per frame), Poisson arrivals at 30 Hz (real
     time): continuous batching over two lanes; p50/p99 from arrival to map on
-    the host, against one plain synchronous call per frame size."""
+    the host and where it goes (queue, device, host), against one plain
+    synchronous call per frame size."""
     import numpy as np
     from paper_2203_02300_gb300 import scenes
     from paper_2203_02300_gb300.serve import run_config4
-    stats, outs, frames = run_config4(frames_per_stream=300, rate_hz=30.0, unique_frames=4, device=device,
-                                      time_scale=time_scale)
+    stats, outs, frames = run_config4(frames_per_stream=300, rate_hz=30.0, device=device,
+                                      time_scale=time_scale, frames=frames, server_kw={"d_chunks": d_chunks})
     plain = {}
     for i, (W, H, D) in enumerate(scenes.STREAMS_CONFIG4):
         l, r = frames[i][0]
         outh = np.empty((H, W), np.int16)
+        p = binding.Params.default(d_chunk=d_chunks[i] if d_chunks else 0)
         for _ in range(3):
-            st.match_host(l.numpy(), r.numpy(), D, out=outh)
+            st.match_host(l.numpy(), r.numpy(), D, p, out=outh)
         ts = []
         for _ in range(20):
             t0 = time.perf_counter()
-            st.match_host(l.numpy(), r.numpy(), D, out=outh)
+            st.match_host(l.numpy(), r.numpy(), D, p, out=outh)
             ts.append((time.perf_counter() - t0) * 1e3)
         plain[f"{W}x{H} D={D}"] = {"p50_ms": statistics.median(ts), "p99_ms": max(ts)}
         assert np.array_equal(outh, outs[(i, 0)]), "served map differs from the plain call"
     stats = dict(stats)
-    stats["per_stream"] = {f"{W}x{H} D={D}": v for (W, H, D), (k, v) in
+    stats["per_stream"] = {f"{W}x{H} D={D} (stream {k})": v for (W, H, D), (k, v) in
                            zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
     return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
-            "frames_per_stream": 300, "rate_hz": 30 * time_scale, **stats, "plain_single_call": plain}
+            "frames_per_stream": 300, "unique_frames_per_stream": len(frames[0]), "rate_hz": 30 * time_scale,
+            "pass_width": d_chunks, **stats, "plain_single_call": plain}
+
+
+def serve_saturation(torch, device: int, frames, d_chunks, seconds: float = 3.0):
+    """Closed loop: every stream keeps its three slots busy for `seconds`;
+    the serving throughput ceiling and the latency at that load."""
+    from paper_2203_02300_gb300.serve import run_saturation
+    st = run_saturation(seconds, device=device, frames=frames, server_kw={"d_chunks": d_chunks})
+    return {"seconds": seconds, "slots_per_stream": 3, "pass_width": d_chunks, **st}
 
 
 # ------------------------------------------------------- oracle timing

@@ -293,12 +293,16 @@ dco_status dco_stereo_densify_stats(dco_stereo *h, int *iters, double *rel_resid
 dco_status dco_stereo_lr_check(dco_stereo *h, const int16_t *dl, const int16_t *dr,
                                int W, int H, int tol, int16_t *out, dco_stream stream);
 
-/* One pair of a batch (all pointers device). */
+/* One pair of a batch (all pointers device).  d_chunk: this pair's pass
+ * width (disparities aggregated per pass, e.g. chosen per shape by an
+ * autotuner); 0 takes p->d_chunk of the call.  Under a workspace budget the
+ * library may narrow it further, as for a single pair. */
 typedef struct {
     const uint8_t *left;
     const uint8_t *right;
     int W, H, D;
     int16_t *disp_out;
+    int d_chunk;
 } dco_pair_desc;
 
 /*

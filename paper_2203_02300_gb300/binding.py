@@ -59,7 +59,7 @@ class DenseParams(ctypes.Structure):
 
 class PairDesc(ctypes.Structure):
     _fields_ = [("left", c_void_p), ("right", c_void_p), ("W", c_int), ("H", c_int), ("D", c_int),
-                ("disp_out", c_void_p)]
+                ("disp_out", c_void_p), ("d_chunk", c_int)]
 
 
 class DcoError(RuntimeError):
@@ -272,13 +272,16 @@ class Stereo:
         return out
 
     def match_batch(self, pairs: Sequence, params: Optional[Params] = None, stream=None):
-        """pairs: sequence of (left, right, D, out) device tensors."""
+        """pairs: sequence of (left, right, D, out) device tensors, or
+        (left, right, D, out, d_chunk) with the pair's own pass width."""
         arr = (PairDesc * len(pairs))()
-        for i, (l, r, D, o) in enumerate(pairs):
+        for i, pr in enumerate(pairs):
+            l, r, D, o = pr[:4]
+            dchunk = int(pr[4]) if len(pr) > 4 and pr[4] else 0
             W, H = _rgb_dims(l)
             _expect(f"pair {i} right", r, l.shape, "uint8", l)
             _expect(f"pair {i} out", o, (H, W), "int16", l)
-            arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o))
+            arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o), dchunk)
         _check(lib().dco_stereo_match_batch(self._h, arr, len(pairs),
                                             ctypes.byref(params) if params else None, _stream(stream)),
                self._h)

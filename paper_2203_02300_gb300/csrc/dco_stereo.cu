@@ -1565,6 +1565,7 @@ struct Job {
     float *cost_l = nullptr, *cost_r = nullptr, *vol = nullptr;
     int vol_view = 0;
     uchar4 *arms0 = nullptr;   // stage entry point: arms of image 0 go here
+    int dchunk = 0;                  // this pair's pass width (0: the call's parameters)
     const int16_t *vsrc = nullptr;   // Eq. 4 round: map voted on (null: no vote)
     int16_t *vdst = nullptr;         //   and the map written
     Layout L{};
@@ -1575,10 +1576,14 @@ struct Job {
 // until the plan fits the handle's budget
 dco_status plan_jobs(dco_stereo *h, const dco_params &p, std::vector<Job> &jobs, size_t &total)
 {
+    // a pair's own pass width (j.dchunk > 0) replaces the call's; a budget
+    // override caps both
     auto plan = [&](int dc_override) {
         size_t t = 0;
         for (auto &j : jobs) {
-            j.L = make_layout(j.W, j.H, j.D, p, dc_override);
+            int dc = j.dchunk > 0 ? j.dchunk : 0;
+            if (dc_override > 0) dc = dc > 0 ? std::min(dc, dc_override) : dc_override;
+            j.L = make_layout(j.W, j.H, j.D, p, dc);
             j.base = t;
             t = align_up(t + j.L.total);
         }
@@ -2320,7 +2325,7 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
     if (n < 0 || (n > 0 && !descs)) return DCO_EINVAL;
     for (int i = 0; i < n; i++)
         if (!descs[i].left || !descs[i].right || !descs[i].disp_out ||
-            !dims_valid(descs[i].W, descs[i].H, descs[i].D))
+            !dims_valid(descs[i].W, descs[i].H, descs[i].D) || descs[i].d_chunk < 0)
             return DCO_EINVAL;
     if (n == 0) return DCO_OK;
     std::vector<Job> jobs(n);
@@ -2328,6 +2333,7 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
         jobs[i].left = descs[i].left; jobs[i].right = descs[i].right;
         jobs[i].W = descs[i].W; jobs[i].H = descs[i].H; jobs[i].D = descs[i].D;
         jobs[i].out = descs[i].disp_out;
+        jobs[i].dchunk = descs[i].d_chunk;
     }
     return run_jobs(h, p, jobs, (cudaStream_t)stream);
 }

@@ -131,7 +131,7 @@ def _disc(rng, W, H, dlo, dhi, texture="fine"):
     return _Surface(cx - r, cy - r, _albedo(texture)(rng, 2 * r + 1, 2 * r + 1), mask, 0.0, 0.0, c)
 
 
-def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset, texture="fine"):
+def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset, texture="fine", fill=None):
     """Z-buffer the surfaces into the left view, forward-warp to the right view."""
     disp = np.full((H, W), -1.0, np.float32)
     left = np.zeros((H, W, 3), np.float32)
@@ -159,7 +159,7 @@ def _render(W, H, surfaces, dclip, rng, noise_sigma, gain, offset, texture="fine
     key = np.full((H, W), -1, np.int64)
     k_src = di * W + xs
     np.maximum.at(key, (ys[inb], xr[inb]), k_src[inb])
-    right = _albedo(texture)(rng, H, W)         # fresh texture fills the holes
+    right = _albedo(texture)(rng, H, W) if fill is None else fill.copy()   # fresh texture fills the holes
     filled = key >= 0
     src_x = key[filled] % W
     right[filled] = left[ys[filled], src_x]
@@ -243,6 +243,7 @@ class StreamScene:
             ang = rng.uniform(0.0, 2.0 * math.pi)
             self.vel.append((speed * math.cos(ang), speed * math.sin(ang)))
         self.rng = rng
+        self.fill = _mixed_texture(np.random.default_rng(self.seed * 31 + 1), H, W)   # the right view's holes
 
     def frame(self, t: int) -> Scene:
         surfaces = [_Surface(0, 0, self.bg, np.ones((self.H, self.W), bool), 0, 0, float(self.dlo))]
@@ -251,7 +252,7 @@ class StreamScene:
                                                 y0=p.y0 + int(round(vy * t))))
         rng = np.random.default_rng(self.seed * 7919 + t)
         left, right, disp, occ = _render(self.W, self.H, surfaces, (self.dlo, self.dhi),
-                                         rng, 2.0, 1.0, 0.0, "mixed")
+                                         rng, 2.0, 1.0, 0.0, "mixed", fill=self.fill)
         return Scene(left, right, disp, occ, self.D)
 
 

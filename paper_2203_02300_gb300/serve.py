@@ -43,6 +43,7 @@ class _Request:
     future: Future
     slot: int = -1
     done: float = 0.0
+    launch: float = 0.0     # when its batch was enqueued
 
 
 class _Slot:
@@ -64,14 +65,24 @@ class _Lane:
 class Server:
     def __init__(self, shapes: Sequence[tuple[int, int, int]], budget_bytes: Optional[int] = None,
                  lanes: int = 2, slots_per_stream: int = 3, max_batch: int = 16,
-                 params: Optional[Params] = None, device: int = 0):
+                 params: Optional[Params] = None, device: int = 0,
+                 d_chunks: Optional[Sequence[int]] = None):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         self.params = params
         self.max_batch = max_batch
-        ws = [Stereo.workspace_bytes(W, H, D, params) for (W, H, D) in self.shapes]
+        # each stream's pass width (e.g. tune.tune_batch); 0 = the params' own
+        self.d_chunks = [int(v) for v in (d_chunks or [0] * len(self.shapes))]
+
+        def ws_of(s):
+            W, H, D = self.shapes[s]
+            p = Params.default(**{f: getattr(params, f) for f, _ in Params._fields_}) if params else Params.default()
+            if self.d_chunks[s]:
+                p.d_chunk = self.d_chunks[s]
+            return Stereo.workspace_bytes(W, H, D, p)
+        ws = [ws_of(s) for s in range(len(self.shapes))]
         if budget_bytes is None:
             budget_bytes = lanes * sum(ws)   # every stream can be in every lane's batch
         self.lane_budget = budget_bytes // lanes
@@ -87,7 +98,7 @@ class Server:
         for s, (W, H, D) in enumerate(self.shapes):
             for sl in self.slots[s]:
                 if used + ws[s] <= self.lane_budget and len(warm) < max_batch:
-                    warm.append((sl.left, sl.right, D, sl.out))
+                    warm.append((sl.left, sl.right, D, sl.out, self.d_chunks[s]))
                     used += ws[s]
         for sl_list in self.slots:
             for sl in sl_list:
@@ -141,10 +152,18 @@ class Server:
             if ls.size:
                 per[s] = {"frames": int(ls.size), "p50_ms": float(np.percentile(ls, 50)),
                           "p99_ms": float(np.percentile(ls, 99))}
+        # where the latency goes: arrival -> batch enqueued (admission and
+        # scheduling), the batch's device time (input copies, match, map
+        # copies), and the rest (host launch overhead, completion hand-off)
+        queue = np.array([r[4] - r[2] for r in self.records]) * 1e3
+        gpu = np.array([r[5] for r in self.records])
+        rest = lat - queue - gpu
+        parts = {k: {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+                 for k, v in (("queue", queue), ("device", gpu), ("host_rest", rest))}
         return {"frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "frames_per_s": lat.size / max(t1 - t0, 1e-9),
                 "batches": self.n_batches, "mean_batch": self.n_frames_batched / max(self.n_batches, 1),
-                "per_stream": per}
+                "per_stream": per, "latency_parts": parts}
 
     # ----------------------------------------------------------- scheduling
     n_batches = 0
@@ -199,13 +218,18 @@ class Server:
                         sl = self.slots[r.stream][r.slot]
                         sl.left.copy_(r.left, non_blocking=True)
                         sl.right.copy_(r.right, non_blocking=True)
-                        pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out))
+                        pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out, self.d_chunks[r.stream]))
+                    t_launch = time.perf_counter()
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev0.record(lane.stream)
                     lane.stereo.match_batch(pairs, self.params, stream=lane.stream)
                     for r in batch:
                         sl = self.slots[r.stream][r.slot]
                         sl.host_out.copy_(sl.out, non_blocking=True)
-                    ev = torch.cuda.Event()
+                    ev = torch.cuda.Event(enable_timing=True)
                     ev.record(lane.stream)
+                    for r in batch:
+                        r.launch = t_launch
             except Exception as exc:   # fail this batch's requests, keep serving
                 lane.stream.synchronize()
                 with self.cv:
@@ -218,7 +242,7 @@ class Server:
             self.n_batches += 1
             self.n_frames_batched += len(batch)
             with self.done_cv:
-                self.inflight.append((lane, ev, batch))
+                self.inflight.append((lane, ev0, ev, batch))
                 self.done_cv.notify_all()
 
     def _complete(self):
@@ -230,14 +254,15 @@ class Server:
                     if self.stop and not self.sched.is_alive():
                         break
                     continue
-                lane, ev, batch = self.inflight.popleft()
+                lane, ev0, ev, batch = self.inflight.popleft()
             ev.synchronize()
             t = time.perf_counter()
+            gpu_ms = ev0.elapsed_time(ev)   # copies in, match, copies out on the lane's stream
             for r in batch:
                 sl = self.slots[r.stream][r.slot]
                 r.done = t
                 r.future.set_result(sl.host_out.numpy().copy())
-                self.records.append((r.stream, r.slot, r.arrival, t))
+                self.records.append((r.stream, r.slot, r.arrival, t, r.launch, gpu_ms))
             with self.cv:
                 for r in batch:
                     self.slots[r.stream][r.slot].busy = False
@@ -245,22 +270,75 @@ class Server:
                 self.cv.notify_all()
 
 
+def _stream_frames(i: int, W: int, H: int, D: int, n: int):
+    from . import scenes
+    st = scenes.StreamScene(i, W, H, D)
+    return [(s.left, s.right) for s in (st.frame(t) for t in range(n))]
+
+
+def render_frames(shapes, n: int, processes: int = 0):
+    """`n` consecutive frames of every stream (planes moving 0-3 px per frame),
+    as pinned host tensors: frames[stream][t] = (left, right).  processes > 0
+    renders the streams in a spawned process pool (safe after CUDA set-up)."""
+    import torch
+    jobs = [(i, W, H, D, n) for i, (W, H, D) in enumerate(shapes)]
+    if processes > 0:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(min(processes, len(jobs)), mp_context=mp.get_context("spawn")) as ex:
+            raw = list(ex.map(_stream_frames, *zip(*jobs)))
+    else:
+        raw = [_stream_frames(*j) for j in jobs]
+    return [[(torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory()) for l, r in fr] for fr in raw]
+
+
+def run_saturation(duration_s: float = 3.0, shapes=None, unique_frames: int = 4, device: int = 0, server_kw=None,
+                   frames=None):
+    """Closed loop: every stream keeps `slots_per_stream` frames in flight
+    (a new frame is submitted as soon as one of its stream completes), for
+    `duration_s` seconds: the server's throughput ceiling, with the latency
+    at that load.  Returns the server stats."""
+    from . import scenes
+    shapes = shapes or scenes.STREAMS_CONFIG4
+    frames = frames or render_frames(shapes, unique_frames)
+    unique_frames = len(frames[0])
+    kw = dict(server_kw or {})
+    depth = kw.get("slots_per_stream", 3)
+    srv = Server(shapes, device=device, **kw)
+    gc.collect()
+    gc.disable()
+    try:
+        t_end = time.perf_counter() + duration_s
+        k = [0] * len(shapes)
+        live = collections.deque()
+        for i in range(len(shapes)):
+            for _ in range(depth):
+                l, r = frames[i][k[i] % unique_frames]
+                live.append((i, srv.submit(i, l, r)))
+                k[i] += 1
+        while live:
+            i, f = live.popleft()
+            f.result(timeout=120)
+            if time.perf_counter() < t_end:
+                l, r = frames[i][k[i] % unique_frames]
+                live.append((i, srv.submit(i, l, r)))
+                k[i] += 1
+    finally:
+        gc.enable()
+    srv.close()
+    return srv.stats()
+
+
 def run_config4(frames_per_stream: int = 300, rate_hz: float = 30.0, time_scale: float = 1.0,
-                unique_frames: int = 6, shapes=None, device: int = 0, server_kw=None):
+                unique_frames: int = 6, shapes=None, device: int = 0, server_kw=None, frames=None):
     """Replay config 4: Poisson arrivals per stream, frames cycled from a few
     rendered ones (planes translating 0-3 px/frame).  time_scale > 1 replays
     faster than real time.  Returns (server stats, outputs by (stream, frame))."""
     import torch
     from . import scenes
     shapes = shapes or scenes.STREAMS_CONFIG4
-    streams = [scenes.StreamScene(i, W, H, D) for i, (W, H, D) in enumerate(shapes)]
-    frames = []
-    for st in streams:
-        fr = []
-        for t in range(unique_frames):
-            s = st.frame(t)
-            fr.append((torch.from_numpy(s.left).pin_memory(), torch.from_numpy(s.right).pin_memory()))
-        frames.append(fr)
+    frames = frames or render_frames(shapes, unique_frames)
+    unique_frames = len(frames[0])
     events = []
     for i in range(len(shapes)):
         arr = scenes.poisson_arrivals(frames_per_stream, rate_hz, scenes.seed_for(4, 100 + i))

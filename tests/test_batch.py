@@ -179,3 +179,28 @@ def test_batch_vh_order_equals_single(env, config3):
     torch.cuda.synchronize()
     for s, (_, _, _, out) in zip(sub, pairs):
         assert np.array_equal(out.cpu().numpy(), _single(env, s, p))
+
+
+def test_batch_with_per_pair_pass_widths(env, config3):
+    # dco_pair_desc.d_chunk: each pair its own pass width (as the autotuner
+    # picks per shape); results equal the pair alone, bit for bit
+    torch, binding, st = env
+    sub = config3[:8]
+    widths = [32, 0, 64, 96, 0, 32, 128, 64]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda"), w) for s, w in zip(sub, widths)]
+    st.match_batch(pairs)
+    torch.cuda.synchronize()
+    for s, pr in zip(sub, pairs):
+        assert np.array_equal(pr[3].cpu().numpy(), _single(env, s))
+
+
+def test_tuner_picks_a_candidate_and_caches_it(env, tmp_path, monkeypatch):
+    torch, binding, st = env
+    from paper_2203_02300_gb300 import tune
+    monkeypatch.setenv("DCO_TUNE_CACHE", str(tmp_path / "tiles.json"))
+    W, H, D = 320, 240, 96
+    won = tune.tune_shape(st, W, H, D, reps=2)
+    assert won in tune.candidates(W, H, D)
+    assert tune.lookup(W, H, D, torch.cuda.get_device_name(0)) == won
+    assert tune.tune_batch(st, [(W, H, D), (W, H, D)]) == [won, won]
