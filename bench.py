@@ -329,10 +329,15 @@ def own_arm(args):
             from paper_2203_02300_gb300.serve import render_frames
             frames4 = render_frames(scenes.STREAMS_CONFIG4, 16, processes=4)
             d4 = tune.tune_batch(st, scenes.STREAMS_CONFIG4, device=local_rank)
-            extras["serve_config4"] = serve_config4(torch, binding, st, local_rank, frames=frames4, d_chunks=d4)
-            extras["serve_config4_5x_rate"] = serve_config4(torch, binding, st, local_rank, time_scale=5.0,
-                                                            frames=frames4, d_chunks=d4)
+            extras["serve_config4"] = serve_config4_native(torch, binding, st, local_rank, frames=frames4,
+                                                           d_chunks=d4)
+            extras["serve_config4_5x_rate"] = serve_config4_native(torch, binding, st, local_rank, time_scale=5.0,
+                                                                   frames=frames4, d_chunks=d4)
             extras["serve_config4_saturation"] = serve_saturation(torch, local_rank, frames4, d4)
+            # the same replay through the Python serving loop, with the plain
+            # single calls of each size and the served == alone check
+            extras["serve_config4_python_loop"] = serve_config4(torch, binding, st, local_rank, frames=frames4,
+                                                                d_chunks=d4)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -692,6 +697,23 @@ def batch_config5(torch, binding, flush, dev, reps: int = 3, budget: int = 1_500
             "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3)}
 
 
+def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, d_chunks=None):
+    """Config 4 through the library's native serving runtime (dco_server_*:
+    scheduler and completion threads in C++, maps copied straight into
+    pinned output buffers); the same replay and comparison as serve_config4."""
+    import numpy as np
+    from paper_2203_02300_gb300 import scenes
+    from paper_2203_02300_gb300.serve import run_config4_native
+    stats, _, frames = run_config4_native(frames_per_stream=300, rate_hz=30.0, device=device, time_scale=time_scale,
+                                          frames=frames, d_chunks=d_chunks)
+    stats = dict(stats)
+    stats["per_stream"] = {f"{W}x{H} D={D} (stream {k})": v for (W, H, D), (k, v) in
+                           zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
+    return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
+            "frames_per_stream": 300, "unique_frames_per_stream": len(frames[0]), "rate_hz": 30 * time_scale,
+            "pass_width": d_chunks, **stats}
+
+
 def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, d_chunks=None):
     """4 camera streams, 300 frames each (cycled from 16 rendered ones per
     stream, planes moving 0-3 px per frame), Poisson arrivals at 30 Hz (real
@@ -725,11 +747,14 @@ def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, fram
             "pass_width": d_chunks, **stats, "plain_single_call": plain}
 
 
-def serve_saturation(torch, device: int, frames, d_chunks, seconds: float = 3.0):
+def serve_saturation(torch, device: int, frames, d_chunks, seconds: float = 3.0, native: bool = True):
     """Closed loop: every stream keeps its three slots busy for `seconds`;
     the serving throughput ceiling and the latency at that load."""
-    from paper_2203_02300_gb300.serve import run_saturation
-    st = run_saturation(seconds, device=device, frames=frames, server_kw={"d_chunks": d_chunks})
+    from paper_2203_02300_gb300.serve import run_saturation, run_saturation_native
+    if native:
+        st = run_saturation_native(seconds, device=device, frames=frames, d_chunks=d_chunks)
+    else:
+        st = run_saturation(seconds, device=device, frames=frames, server_kw={"d_chunks": d_chunks})
     return {"seconds": seconds, "slots_per_stream": 3, "pass_width": d_chunks, **st}
 
 

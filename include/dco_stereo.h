@@ -396,6 +396,68 @@ dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_t *right, i
  */
 dco_status dco_stereo_noalloc_status(dco_stream stream);
 
+/*
+ * Native serving runtime: frames of several camera streams, each of its own
+ * W x H x D (and pass width), submitted from host memory and matched by
+ * continuous batching.  A scheduler thread admits pending frames in arrival
+ * order into a batch while the frame's stream has a free device slot and the
+ * batch's workspace (dco_stereo_workspace_bytes of its frames) fits a lane's
+ * share of the memory budget, and runs the batch on a free lane: a handle
+ * with its own workspace and CUDA stream copies the images in, runs
+ * dco_stereo_match_batch (the whole path of dco_stereo_match for every
+ * frame) and copies each map straight into the caller's buffer.  Frames that
+ * arrive while other batches are on the device are admitted as slots and
+ * lanes free up, so their work overlaps on the device.  A completion thread
+ * retires each lane's batches on their events and wakes the callers.
+ * Results equal dco_stereo_match on each frame alone (bit for bit).
+ *
+ * dco_server_create: streams[nstreams] the stream shapes (d_chunk 0: the
+ *   params' pass width); lanes 1..16; slots_per_stream >= 1 (frames of one
+ *   stream in flight at once); max_batch >= 1 frames per batch;
+ *   budget_bytes the device workspace of all lanes together (0: every
+ *   stream's frame in every lane's batch).  The server allocates its slots
+ *   and warms every lane up before returning (no allocation while serving).
+ *   DCO_EBUDGET if a lane's share cannot hold one frame of the largest
+ *   stream.
+ * dco_server_submit: left, right (W*H*3 bytes) and disp_out (W*H int16) are
+ *   host buffers of the stream's shape (pinned memory makes the copies
+ *   asynchronous) that must stay valid until dco_server_wait returns for
+ *   the ticket; returns at once with the request's ticket.
+ * dco_server_wait: blocks until the request is done (timeout_ms < 0: no
+ *   limit; DCO_ETIMEOUT when the limit passes first, the request still
+ *   pending), fills *times (may be NULL) and returns the request's status
+ *   (a failed batch fails its requests; the server keeps serving).  Each
+ *   ticket is waited for once.
+ * dco_server_destroy: launches and retires every pending frame, then frees
+ *   the server.
+ * The paper has no counterpart: this is the serving pattern of the
+ * matcher's deployment (several camera streams, Sect. 7's mixed-reality
+ * use).
+ */
+typedef struct dco_server dco_server;
+typedef struct {
+    int W, H, D;
+    int d_chunk;
+} dco_stream_desc;
+typedef struct {
+    double arrival_s;  /* submit time, steady clock seconds */
+    double launch_s;   /* its batch was enqueued on a lane */
+    double done_s;     /* the completion thread saw the batch finish */
+    float device_ms;   /* the batch's copies and match on the lane's stream */
+} dco_request_times;
+
+dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc *streams, int nstreams,
+                             int lanes, int slots_per_stream, int max_batch, size_t budget_bytes,
+                             const dco_params *p);
+dco_status dco_server_submit(dco_server *s, int stream, const uint8_t *left, const uint8_t *right,
+                             int16_t *disp_out, unsigned long long *ticket);
+dco_status dco_server_wait(dco_server *s, unsigned long long ticket, int timeout_ms, dco_request_times *times);
+/* batches launched, frames in them, the largest batch workspace and a lane's
+ * budget share (any pointer may be NULL) */
+dco_status dco_server_counters(dco_server *s, unsigned long long *batches, unsigned long long *frames,
+                               size_t *max_batch_bytes, size_t *lane_budget);
+void dco_server_destroy(dco_server *s);
+
 /* Text of the last CUDA or budget error seen by the handle ("" if none).
  * Owned by the handle, valid until its next call. */
 const char *dco_stereo_last_error(dco_stereo *h);

@@ -62,6 +62,15 @@ class PairDesc(ctypes.Structure):
                 ("disp_out", c_void_p), ("d_chunk", c_int)]
 
 
+class StreamDesc(ctypes.Structure):
+    _fields_ = [("W", c_int), ("H", c_int), ("D", c_int), ("d_chunk", c_int)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("launch_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("device_ms", c_float)]
+
+
 class DcoError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -121,6 +130,11 @@ def lib():
             "dco_stereo_set_test_flags": (c_int, [P, c_int]),
             "dco_stereo_workspace_allocated": (c_size_t, [P]),
             "dco_stereo_batch_groups": (c_int, [P]),
+            "dco_server_create": (c_int, [P, c_int, P, c_int, c_int, c_int, c_int, c_size_t, P]),
+            "dco_server_submit": (c_int, [P, c_int, P, P, P, P]),
+            "dco_server_wait": (c_int, [P, ctypes.c_ulonglong, c_int, P]),
+            "dco_server_counters": (c_int, [P, P, P, P, P]),
+            "dco_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -429,3 +443,65 @@ class Stereo:
                                                 ctypes.byref(ms)), self._h)
             res[name.value.decode()] = (cnt.value, ms.value)
         return res
+
+
+class NativeServer:
+    """The library's serving runtime (dco_server_*): continuous batching of
+    frames from several camera streams, scheduled and retired by native
+    threads.  submit() takes host uint8 (H, W, 3) images and an int16 (H, W)
+    output buffer of the stream's shape (pinned numpy arrays make the copies
+    asynchronous) and returns a ticket; wait(ticket) blocks until the map is
+    in the output buffer and returns the request's times."""
+
+    def __init__(self, shapes, device: int = 0, lanes: int = 2, slots_per_stream: int = 3, max_batch: int = 16,
+                 budget_bytes: int = 0, params: Optional[Params] = None, d_chunks=None):
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        dcs = [int(v) for v in (d_chunks or [0] * len(self.shapes))]
+        arr = (StreamDesc * len(self.shapes))(*[StreamDesc(W, H, D, dc) for (W, H, D), dc in zip(self.shapes, dcs)])
+        self._s = c_void_p()
+        self._keep = {}
+        _check(lib().dco_server_create(ctypes.byref(self._s), device, arr, len(self.shapes), lanes, slots_per_stream,
+                                       max_batch, budget_bytes, ctypes.byref(params) if params else None), None)
+
+    def submit(self, stream: int, left: np.ndarray, right: np.ndarray, out: np.ndarray) -> int:
+        W, H, _ = self.shapes[stream]
+        _expect("left", left, (H, W, 3), "uint8")
+        _expect("right", right, (H, W, 3), "uint8")
+        _expect("out", out, (H, W), "int16")
+        t = ctypes.c_ulonglong()
+        _check(lib().dco_server_submit(self._s, stream, _ptr(left), _ptr(right), _ptr(out), ctypes.byref(t)), None)
+        self._keep[t.value] = (left, right, out)   # the buffers stay alive until the wait
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> RequestTimes:
+        tm = RequestTimes()
+        rc = lib().dco_server_wait(self._s, ticket, timeout_ms, ctypes.byref(tm))
+        if rc != DCO_ETIMEOUT:
+            self._keep.pop(ticket, None)
+        _check(rc, None)
+        return tm
+
+    def counters(self) -> dict:
+        b, f = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        mb, lb = c_size_t(), c_size_t()
+        _check(lib().dco_server_counters(self._s, ctypes.byref(b), ctypes.byref(f), ctypes.byref(mb),
+                                         ctypes.byref(lb)), None)
+        return {"batches": b.value, "frames": f.value, "max_batch_bytes": mb.value, "lane_budget": lb.value}
+
+    def close(self) -> None:
+        if self._s:
+            lib().dco_server_destroy(self._s)
+            self._s = c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

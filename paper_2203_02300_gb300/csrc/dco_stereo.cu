@@ -2535,3 +2535,6 @@ extern "C" dco_status dco_stereo_noalloc_status(dco_stream stream)
     }
     return status_of_word(v);
 }
+
+// ====================================================== serving runtime
+#include "serve.cuh"

@@ -363,3 +363,133 @@ def run_config4(frames_per_stream: int = 300, rate_hz: float = 30.0, time_scale:
         gc.enable()
     srv.close()
     return srv.stats(), outs, frames
+
+
+# ------------------------------------------------------------ native runtime
+def _native_stats(records, nstreams: int, counters: dict) -> dict:
+    """records: (stream, arrival_s, launch_s, done_s, device_ms) per frame."""
+    lat = np.array([r[3] - r[1] for r in records]) * 1e3
+    if lat.size == 0:
+        return {"frames": 0}
+    queue = np.array([r[2] - r[1] for r in records]) * 1e3
+    dev = np.array([r[4] for r in records])
+    rest = lat - queue - dev
+    t0 = min(r[1] for r in records)
+    t1 = max(r[3] for r in records)
+    per = {}
+    for s in range(nstreams):
+        ls = np.array([r[3] - r[1] for r in records if r[0] == s]) * 1e3
+        if ls.size:
+            per[s] = {"frames": int(ls.size), "p50_ms": float(np.percentile(ls, 50)),
+                      "p99_ms": float(np.percentile(ls, 99))}
+    parts = {k: {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+             for k, v in (("queue", queue), ("device", dev), ("host_rest", rest))}
+    return {"frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "frames_per_s": lat.size / max(t1 - t0, 1e-9), "batches": counters["batches"],
+            "mean_batch": counters["frames"] / max(counters["batches"], 1), "per_stream": per,
+            "latency_parts": parts, "runtime": "native"}
+
+
+def run_config4_native(frames_per_stream: int = 300, rate_hz: float = 30.0, time_scale: float = 1.0,
+                       unique_frames: int = 6, shapes=None, device: int = 0, frames=None, d_chunks=None,
+                       keep_outputs: bool = False, server_kw=None):
+    """Config 4 replayed through the library's native serving runtime
+    (dco_server_*): Poisson arrivals per stream, each frame's map copied by
+    the server straight into a pinned output buffer.  Returns (stats,
+    outputs by (stream, frame) if keep_outputs, frames)."""
+    import torch
+    from . import scenes
+    from .binding import NativeServer
+    shapes = shapes or scenes.STREAMS_CONFIG4
+    frames = frames or render_frames(shapes, unique_frames)
+    unique_frames = len(frames[0])
+    events = []
+    for i in range(len(shapes)):
+        arr = scenes.poisson_arrivals(frames_per_stream, rate_hz, scenes.seed_for(4, 100 + i))
+        events += [(t / time_scale, i, k) for k, t in enumerate(arr)]
+    events.sort()
+    kw = dict(server_kw or {})
+    slots = kw.get("slots_per_stream", 3)
+    # output buffers: every frame its own when kept, else a ring per stream
+    # deeper than the frames a stream can have in flight
+    ring = 4 * slots
+
+    def out_buf(i, k):
+        W, H, _ = shapes[i]
+        return torch.empty((H, W), dtype=torch.int16).pin_memory().numpy()
+    outs = {} if keep_outputs else {(i, j): out_buf(i, j) for i in range(len(shapes)) for j in range(ring)}
+    srv = NativeServer(shapes, device=device, d_chunks=d_chunks, **kw)
+    tickets = [collections.deque() for _ in shapes]   # per stream, oldest first
+    records = []
+
+    def retire(i):
+        tm = srv.wait(tickets[i].popleft())
+        records.append((i, tm.arrival_s, tm.launch_s, tm.done_s, tm.device_ms))
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for t, i, k in events:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            while len(tickets[i]) >= ring:   # the ring buffer about to be reused is free
+                retire(i)
+            l, r = frames[i][k % unique_frames]
+            if keep_outputs:
+                outs[(i, k)] = out_buf(i, k)
+                o = outs[(i, k)]
+            else:
+                o = outs[(i, k % ring)]
+            tickets[i].append(srv.submit(i, l.numpy(), r.numpy(), o))
+        for i in range(len(shapes)):
+            while tickets[i]:
+                retire(i)
+    finally:
+        gc.enable()
+    cnt = srv.counters()
+    srv.close()
+    return _native_stats(records, len(shapes), cnt), (outs if keep_outputs else None), frames
+
+
+def run_saturation_native(duration_s: float = 3.0, shapes=None, unique_frames: int = 4, device: int = 0,
+                          frames=None, d_chunks=None, server_kw=None):
+    """Closed loop through the native runtime: every stream keeps its slots
+    busy (a new frame as soon as one of the stream completes) for
+    `duration_s` seconds."""
+    import torch
+    from . import scenes
+    from .binding import NativeServer
+    shapes = shapes or scenes.STREAMS_CONFIG4
+    frames = frames or render_frames(shapes, unique_frames)
+    unique_frames = len(frames[0])
+    kw = dict(server_kw or {})
+    depth = kw.get("slots_per_stream", 3)
+    srv = NativeServer(shapes, device=device, d_chunks=d_chunks, **kw)
+    bufs = {(i, j): torch.empty((shapes[i][1], shapes[i][0]), dtype=torch.int16).pin_memory().numpy()
+            for i in range(len(shapes)) for j in range(depth)}
+    records = []
+    gc.collect()
+    gc.disable()
+    try:
+        t_end = time.perf_counter() + duration_s
+        k = [0] * len(shapes)
+        live = collections.deque()
+        for i in range(len(shapes)):
+            for j in range(depth):
+                l, r = frames[i][k[i] % unique_frames]
+                live.append((i, j, srv.submit(i, l.numpy(), r.numpy(), bufs[(i, j)])))
+                k[i] += 1
+        while live:
+            i, j, tk = live.popleft()
+            tm = srv.wait(tk)
+            records.append((i, tm.arrival_s, tm.launch_s, tm.done_s, tm.device_ms))
+            if time.perf_counter() < t_end:
+                l, r = frames[i][k[i] % unique_frames]
+                live.append((i, j, srv.submit(i, l.numpy(), r.numpy(), bufs[(i, j)])))
+                k[i] += 1
+    finally:
+        gc.enable()
+    cnt = srv.counters()
+    srv.close()
+    return _native_stats(records, len(shapes), cnt)

@@ -90,3 +90,66 @@ def test_config4_full_size_streams_against_the_oracle(env):
         if k == 0:
             ref = O.match(l.numpy(), r.numpy(), D)
             parity.check_final(got, ref, f"config 4 stream {i} ({W}x{H} D={D}) frame 0 final map")
+
+
+def test_native_runtime_results_equal_alone(env):
+    # the library's serving runtime (dco_server_*): frames of three streams at
+    # 400 Hz each, every map equal to the frame matched alone
+    from paper_2203_02300_gb300.serve import run_config4_native
+    stats, outs, frames = run_config4_native(frames_per_stream=16, rate_hz=400.0, unique_frames=4, shapes=SHAPES,
+                                             keep_outputs=True)
+    alone = _alone(env, frames)
+    for (i, k), got in outs.items():
+        assert np.array_equal(got, alone[(i, k % 4)]), (i, k)
+    assert stats["frames"] == 16 * len(SHAPES)
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert stats["latency_parts"]["device"]["p50_ms"] > 0
+
+
+def test_native_runtime_batches_a_burst_within_the_budget(env):
+    torch, binding, st = env
+    from paper_2203_02300_gb300 import scenes
+    frames = [[(torch.from_numpy(s.left).pin_memory().numpy(), torch.from_numpy(s.right).pin_memory().numpy())
+               for s in [scenes.StreamScene(i, W, H, D).frame(t) for t in range(2)]]
+              for i, (W, H, D) in enumerate(SHAPES)]
+    ws = [binding.Stereo.workspace_bytes(W, H, D) for (W, H, D) in SHAPES]
+    budget = 2 * (ws[2] + ws[1])
+    outs, tickets = [], []
+    with binding.NativeServer(SHAPES, budget_bytes=budget, lanes=2, slots_per_stream=2, max_batch=8) as srv:
+        for rep in range(3):
+            for i, (W, H, D) in enumerate(SHAPES):
+                for k in range(2):
+                    o = torch.full((H, W), -9, dtype=torch.int16).pin_memory().numpy()
+                    outs.append(((i, k), o))
+                    tickets.append(srv.submit(i, frames[i][k][0], frames[i][k][1], o))
+        for t in tickets:
+            srv.wait(t, timeout_ms=60000)
+        cnt = srv.counters()
+    alone = {}
+    for i, (W, H, D) in enumerate(SHAPES):
+        for k in range(2):
+            alone[(i, k)] = st.match(torch.from_numpy(frames[i][k][0]).cuda(), torch.from_numpy(frames[i][k][1]).cuda(),
+                                     D).cpu().numpy()
+    for key, got in outs:
+        assert np.array_equal(got, alone[key])
+    assert cnt["frames"] == 18 and cnt["frames"] / cnt["batches"] > 1.0   # a burst is served in batches
+    assert 0 < cnt["max_batch_bytes"] <= cnt["lane_budget"] == budget // 2
+
+
+def test_native_runtime_rejects_bad_requests(env):
+    torch, binding, st = env
+    import pytest as _pt
+    with binding.NativeServer(SHAPES[:1]) as srv:
+        W, H, _ = SHAPES[0]
+        l = np.zeros((H, W, 3), np.uint8)
+        o = np.zeros((H, W), np.int16)
+        with _pt.raises(binding.DcoError) as e:
+            binding._check(binding.lib().dco_server_submit(srv._s, 5, l.ctypes.data, l.ctypes.data, o.ctypes.data,
+                                                           binding.ctypes.byref(binding.ctypes.c_ulonglong())), None)
+        assert e.value.code == binding.DCO_EINVAL
+        with _pt.raises(binding.DcoError) as e:
+            srv.wait(12345)
+        assert e.value.code == binding.DCO_EINVAL
+    with _pt.raises(binding.DcoError) as e:   # a lane's share cannot hold one frame
+        binding.NativeServer(SHAPES, budget_bytes=1000)
+    assert e.value.code == binding.DCO_EBUDGET
