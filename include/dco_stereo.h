@@ -27,7 +27,9 @@
  *   - A handle owns one workspace.  Calls on one handle must not run
  *     concurrently (use one handle per stream that works in parallel).
  *   - Argument errors return DCO_EINVAL before anything is enqueued.
- *     Limits: 1 <= W, H <= 16384; 1 <= D <= 256; D <= W; 1 <= arm_l1 <= 40;
+ *     Limits: 1 <= W, H <= 16384; 1 <= D; 0 <= p->d_min; d_min + D <= 256
+ *     and <= W (D counts the disparities searched, d_min + D - 1 is the
+ *     largest; maps hold absolute disparities); 1 <= arm_l1 <= 40;
  *     census window odd, at most 64 bits; lambda_ad, lambda_census, eps > 0;
  *     gamma_l >= 0.
  *   - A workspace the device cannot allocate returns DCO_ENOMEM (one beyond
@@ -108,6 +110,7 @@ typedef struct {
     int vote_iters; /* Eq. 4 rounds after the consistency check (0 = none) */
     int smooth_arms; /* 1: smooth cross-support window (Sect. 4.1), see above; 0 = raw arms */
     int agg_order; /* 0: horizontal then vertical sums (Eq. 2); 1: vertical then horizontal */
+    int d_min; /* smallest disparity searched (Eq. 3's d_min): d in [d_min, d_min + D - 1]; 0 */
 } dco_params;
 
 /* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */

@@ -33,7 +33,8 @@
  *     horizontal segment; N = its pixel count.  Reference-view arms only.
  *     The other order (union over q on p's horizontal arm of q's vertical
  *     segment) is available as a variant.
- *   - d in [0, D-1]; a match outside the image costs 1 (upper bound of Eq. 1).
+ *   - d in [d_min, d_min + D - 1] (Eq. 3's [d_min, d_max], D values; d_min = 0
+ *     by default); a match outside the image costs 1 (upper bound of Eq. 1).
  *   - WTA (Eq. 3) takes the smallest d among equal minima.
  *   - the decision in the kernel's precision (optional outputs qdisp_*):
  *     the paper fixes no precision, so where floating point decides the
@@ -217,6 +218,7 @@ double orc_cost_terms(int ad_sum, int ham, int lmin, double lambda_ad, double la
 
 typedef struct {
     int W, H, D;
+    int dmin;                           /* d in [dmin, dmin + D - 1] */
     const uint8_t *ref_rgb, *oth_rgb;   /* reference view and the other view */
     const uint64_t *ref_cen, *oth_cen;
     const uint8_t *ref_arms;
@@ -339,7 +341,7 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
     if (qdisp)
         for (long i = 0; i < (long)W * no; i++) { qbest[i] = UINT64_MAX; qdisp[i] = 0; }
 
-    for (int d = 0; d < v->D; d++) {
+    for (int d = v->dmin; d < v->dmin + v->D; d++) {
 #pragma omp parallel for schedule(static)
         for (int y = ya; y < yb; y++)
             for (int x = 0; x < W; x++) C[(long)(y - ya) * W + x] = pixel_cost(v, x, y, d);
@@ -392,7 +394,7 @@ static int run_view(const view_ctx *v, int y0, int y1, int reach, int16_t *disp,
                     for (int xx = x - a[0]; xx <= x + a[1]; xx++) s += SH[(long)(y - ya) * W + xx];
                 long i = (long)(y - y0) * W + x;
                 double cbar = s / (double)N[i];
-                if (vol) vol[(long)d * W * no + i] = cbar;
+                if (vol) vol[(long)(d - v->dmin) * W * no + i] = cbar;
                 if (cbar < best[i]) { second[i] = best[i]; best[i] = cbar; disp[i] = (int16_t)d; }
                 else if (cbar < second[i]) { second[i] = cbar; }
                 if (qdisp) {
@@ -432,14 +434,15 @@ int orc_lr_check(const int16_t *dl, const int16_t *dr, int W, int rows, int tol,
 }
 
 /*
- * Full matcher on rows [y0, y1) of a W x H pair with D disparities.
- * Every output array holds (y1 - y0) x W values; vol_l / vol_r (optional)
- * hold D x (y1 - y0) x W aggregated costs.  Census and arms are computed on
+ * Full matcher on rows [y0, y1) of a W x H pair with the D disparities
+ * dmin .. dmin + D - 1.  Every output array holds (y1 - y0) x W values;
+ * vol_l / vol_r (optional) hold D x (y1 - y0) x W aggregated costs, plane k
+ * for disparity dmin + k.  Census and arms are computed on
  * the whole image (they are cheap next to the aggregation).  qdisp_l /
  * qdisp_r (optional, both or neither) receive the Eq. 3 decisions taken in
  * the kernel's precision (header); disp_* are the FP64 decisions.
  */
-int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
+int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D, int dmin,
               double lambda_ad, double lambda_census, double gamma_l, double eps,
               int cw, int ch, int L1, int L2, int tau1, int tau2, int lr_tol, int smooth, int order,
               int y0, int y1,
@@ -447,7 +450,8 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
               double *best_l, double *second_l, double *best_r, double *second_r,
               double *vol_l, double *vol_r, int16_t *qdisp_l, int16_t *qdisp_r)
 {
-    if (!left || !right || W < 1 || H < 1 || D < 1 || y0 < 0 || y1 > H || y0 > y1) return ORC_EINVAL;
+    if (!left || !right || W < 1 || H < 1 || D < 1 || dmin < 0 || y0 < 0 || y1 > H || y0 > y1)
+        return ORC_EINVAL;
     if (!disp_l || !disp_r || !disp_final || !best_l || !second_l || !best_r || !second_r)
         return ORC_EINVAL;
     size_t npx = (size_t)W * H;
@@ -467,8 +471,8 @@ int orc_match(const uint8_t *left, const uint8_t *right, int W, int H, int D,
         orc_cost_params cp = {lambda_ad, lambda_census, gamma_l, eps};
         view_ctx *vl = (view_ctx *)calloc(1, sizeof(view_ctx)), *vr = (view_ctx *)calloc(1, sizeof(view_ctx));
         if (!vl || !vr) { free(vl); free(vr); rc = ORC_ENOMEM; goto done; }
-        *vl = (view_ctx){W, H, D, left, right, cl, cr, al, -1, cp, order};
-        *vr = (view_ctx){W, H, D, right, left, cr, cl, ar, +1, cp, order};
+        *vl = (view_ctx){W, H, D, dmin, left, right, cl, cr, al, -1, cp, order};
+        *vr = (view_ctx){W, H, D, dmin, right, left, cr, cl, ar, +1, cp, order};
         if (qdisp_l && qdisp_r) { quant_tables(vl, L1); quant_tables(vr, L1); }
         rc = run_view(vl, y0, y1, L1, disp_l, best_l, second_l, vol_l, qdisp_l && qdisp_r ? qdisp_l : NULL);
         if (rc == ORC_OK)
@@ -485,15 +489,16 @@ done:
 /*
  * Parallax optimisation (Sect. 4.3, Eq. 4): `iters` rounds of
  *   d'(p) = argmax_d hist(d, N_p)
- * on a W x H map with disparities in [0, D-1] (-1 = invalid), N_p being the
+ * on a W x H map with disparities in [dmin, dmin + D - 1] (any other value,
+ * -1 after the consistency check, is invalid and casts no vote), N_p being the
  * support region of Eq. 2 built from `arms` (4 bytes per pixel: l, r, u, d).
  * The histogram counts every pixel of the region explicitly (pixels of the
  * region are enumerated row by row; the region is a union of disjoint row
  * segments, so no pixel is counted twice).
  */
-int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int iters, int16_t *out)
+int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int dmin, int iters, int16_t *out)
 {
-    if (!disp || !arms || !out || W < 1 || H < 1 || D < 1 || iters < 0) return ORC_EINVAL;
+    if (!disp || !arms || !out || W < 1 || H < 1 || D < 1 || dmin < 0 || iters < 0) return ORC_EINVAL;
     long n = (long)W * H;
     int16_t *cur = (int16_t *)malloc(sizeof(int16_t) * n);
     int16_t *nxt = (int16_t *)malloc(sizeof(int16_t) * n);
@@ -507,20 +512,20 @@ int orc_vote(const int16_t *disp, const uint8_t *arms, int W, int H, int D, int 
             if (!hist) { rc = ORC_ENOMEM; continue; }
             for (int x = 0; x < W; x++) {
                 long i = (long)y * W + x;
-                if (cur[i] < 0 || cur[i] >= D) { nxt[i] = -1; continue; }   /* invalid */
+                if (cur[i] < dmin || cur[i] >= dmin + D) { nxt[i] = -1; continue; }   /* invalid */
                 for (int d = 0; d < D; d++) hist[d] = 0;
                 const uint8_t *ap = arms + 4 * i;
                 for (int yy = y - ap[2]; yy <= y + ap[3]; yy++) {
                     const uint8_t *aq = arms + 4 * ((long)yy * W + x);
                     for (int xx = x - aq[0]; xx <= x + aq[1]; xx++) {
                         int v = cur[(long)yy * W + xx];
-                        if (v >= 0 && v < D) hist[v]++;
+                        if (v >= dmin && v < dmin + D) hist[v - dmin]++;
                     }
                 }
                 int best = 0;
                 for (int d = 1; d < D; d++)
                     if (hist[d] > hist[best]) best = d;   /* strict: smallest d on ties */
-                nxt[i] = (int16_t)best;
+                nxt[i] = (int16_t)(dmin + best);
             }
             free(hist);
         }

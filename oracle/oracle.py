@@ -41,10 +41,10 @@ def lib():
         L.orc_cost_terms.argtypes = [i, i, i, d, d, d, d]
         L.orc_cost_terms.restype = d
         L.orc_lr_check.argtypes = [P, P, i, i, i, P]
-        L.orc_match.argtypes = [P, P, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i, i] + [P] * 11
+        L.orc_match.argtypes = [P, P, i, i, i, i, d, d, d, d, i, i, i, i, i, i, i, i, i, i, i] + [P] * 11
         L.orc_arms_smooth.argtypes = [P, i, i, P]
         L.orc_arms_smooth.restype = i
-        L.orc_vote.argtypes = [P, P, i, i, i, i, P]
+        L.orc_vote.argtypes = [P, P, i, i, i, i, i, P]
         L.orc_vote.restype = i
         L.orc_downscale.argtypes = [P, i, i, P]
         L.orc_downscale.restype = i
@@ -76,6 +76,7 @@ class Params:
     lr_tol: int = 1               # reading; < 0 disables the check
     smooth_arms: int = 0          # reading of Sect. 4.1's morphological processing; 1 = 3x3 opening
     agg_order: int = 0            # 0: region H then V (Eq. 2 reading); 1: V then H (variant)
+    d_min: int = 0                # Eq. 3: d in [d_min, d_min + D - 1]
 
 
 def _ptr(a: np.ndarray):
@@ -151,16 +152,17 @@ def lr_check(dl: np.ndarray, dr: np.ndarray, tol: int = 1) -> np.ndarray:
     return out
 
 
-def vote(disp: np.ndarray, arm: np.ndarray, D: int, iters: int = 1) -> np.ndarray:
+def vote(disp: np.ndarray, arm: np.ndarray, D: int, iters: int = 1, d_min: int = 0) -> np.ndarray:
     """Parallax optimisation (Sect. 4.3, Eq. 4): `iters` rounds of the mode of
-    the valid disparities over each valid pixel's support region (arms of
-    the reference view, (H, W, 4) uint8 l, r, u, d)."""
+    the valid disparities (those in [d_min, d_min + D - 1]) over each valid
+    pixel's support region (arms of the reference view, (H, W, 4) uint8 l, r,
+    u, d)."""
     disp = np.ascontiguousarray(disp, np.int16)
     arm = np.ascontiguousarray(arm, np.uint8)
     H, W = disp.shape
     assert arm.shape == (H, W, 4)
     out = np.empty_like(disp)
-    _check(lib().orc_vote(_ptr(disp), _ptr(arm), W, H, D, iters, _ptr(out)))
+    _check(lib().orc_vote(_ptr(disp), _ptr(arm), W, H, D, d_min, iters, _ptr(out)))
     return out
 
 
@@ -192,7 +194,7 @@ class MatchResult:
     second_l: np.ndarray   # (rows, W) float64 second-smallest aggregated cost
     best_r: np.ndarray
     second_r: np.ndarray
-    vol_l: Optional[np.ndarray] = None   # (D, rows, W) aggregated costs
+    vol_l: Optional[np.ndarray] = None   # (D, rows, W) aggregated costs, plane k for d = d_min + k
     vol_r: Optional[np.ndarray] = None
     y0: int = 0
     # Eq. 3 decisions taken in the kernel's precision (FP32 Eq. 1, fixed
@@ -224,7 +226,7 @@ def match(left: np.ndarray, right: np.ndarray, D: int, p: Params = Params(),
     ql = np.empty((n, W), np.int16) if quantized else None
     qr = np.empty((n, W), np.int16) if quantized else None
     null = ctypes.c_void_p(0)
-    _check(lib().orc_match(_ptr(left), _ptr(right), W, H, D, p.lambda_ad, p.lambda_census,
+    _check(lib().orc_match(_ptr(left), _ptr(right), W, H, D, p.d_min, p.lambda_ad, p.lambda_census,
                            p.gamma_l, p.eps, p.census_w, p.census_h, p.arm_l1, p.arm_l2,
                            p.tau1, p.tau2, p.lr_tol, p.smooth_arms, p.agg_order, y0, y1,
                            _ptr(dl), _ptr(dr), _ptr(df), _ptr(bl), _ptr(sl), _ptr(br), _ptr(sr),

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
                 ("eps", c_float), ("census_w", c_int), ("census_h", c_int), ("arm_l1", c_int),
                 ("arm_l2", c_int), ("tau1", c_int), ("tau2", c_int), ("lr_tol", c_int),
                 ("d_chunk", c_int), ("vote_iters", c_int), ("smooth_arms", c_int),
-                ("agg_order", c_int)]
+                ("agg_order", c_int), ("d_min", c_int)]
 
     @classmethod
     def default(cls, **over) -> "Params":

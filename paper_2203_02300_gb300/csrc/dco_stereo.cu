@@ -930,7 +930,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
                 const uint32_t n = NQ[r + fwd()] - (lo >= 0 ? NQ[lo] : 0u);
                 for (int j = 0; j < nlive; j++) {
                     const uint32_t vv = qh[j] - ql[j];
-                    a.vol[(size_t)(dbase + j) * H * W + pix(ya + r)] = float(vv) / (float(n) * a.S);
+                    a.vol[(size_t)(dbase - a.dmin + j) * H * W + pix(ya + r)] = float(vv) / (float(n) * a.S);
                 }
             }
         }
@@ -949,7 +949,7 @@ __device__ __forceinline__ void vagg_body(const VArgs &a, int bx, int by, int bz
         key = prev <= key ? prev : key;   // earlier passes hold smaller d
     }
     if (a.last) {
-        const bool invalid = kMax && (a.mask[i] < 0 || a.mask[i] >= a.D);   // Eq. 4: no vote, stays invalid
+        const bool invalid = kMax && (a.mask[i] < a.dmin || a.mask[i] >= a.D);   // Eq. 4: no vote, stays invalid
         disp[i] = invalid ? (int16_t)-1 : (int16_t)(key & 0xffffffffu);
         if (cost) {
             const int lo = r - back() - 1;
@@ -1139,6 +1139,7 @@ struct Derived {
     uint32_t Sint;
     float S;
     int order;   // aggregation order: 0 horizontal then vertical, 1 vertical then horizontal
+    int dmin;    // smallest disparity of the search
 };
 
 struct Layout {
@@ -1160,6 +1161,7 @@ bool derive(const dco_params &p, Derived &d)
     d.Sint = (uint32_t)s;
     d.S = (float)s;
     d.order = p.agg_order;
+    d.dmin = p.d_min;
     return true;
 }
 
@@ -1174,12 +1176,13 @@ bool params_valid(const dco_params &p)
     if (p.vote_iters < 0 || p.vote_iters > 64) return false;
     if (p.smooth_arms != 0 && p.smooth_arms != 1) return false;
     if (p.agg_order != 0 && p.agg_order != 1) return false;
+    if (p.d_min < 0 || p.d_min > 255) return false;
     return true;
 }
 
-bool dims_valid(int W, int H, int D)
+bool dims_valid(int W, int H, int D, int dmin = 0)
 {
-    return W >= 1 && H >= 1 && W <= 16384 && H <= 16384 && D >= 1 && D <= 256 && D <= W;
+    return W >= 1 && H >= 1 && W <= 16384 && H <= 16384 && D >= 1 && dmin >= 0 && dmin + D <= 256 && dmin + D <= W;
 }
 
 Layout make_layout(int W, int H, int D, const dco_params &p, int dc_override = 0)
@@ -1733,7 +1736,7 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
     const bool vh = dv.order == 1;   // vertical segment sums first (k_vcost), then rows (k_vagg<.., kRow>)
     for (const Job &j : jobs) {
         if (pass >= j.L.npass) continue;
-        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
+        const int d0 = dv.dmin + pass * j.L.dc, dc = std::min(j.L.dc, dv.dmin + j.D - d0);
         const HGeom hg = vh ? vcost_geom(j.W, j.H, dc, dv.L1) : hagg_geom(j.W, j.H, dc, dv.L1);
         const VGeom vg = vh ? vagg_geom(j.H, j.W, dv.L1) : vagg_geom(j.W, j.H, dv.L1);
         hsm[hg.nw] = std::max(hsm[hg.nw], hg.smem);
@@ -1745,7 +1748,7 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
             a.a.sh[v] = jptr<uint32_t>(h, j, j.L.sh[v]);
         }
         a.a.tables = h->d_tables;
-        a.a.W = j.W; a.a.H = j.H; a.a.D = j.D; a.a.rpitch = j.L.rpitch;
+        a.a.W = j.W; a.a.H = j.H; a.a.D = dv.dmin + j.D; a.a.rpitch = j.L.rpitch;
         a.a.d0 = d0; a.a.dc = dc; a.a.dstride = j.L.dstride;
         a.a.ngroups = (dc + 31) / 32;
         a.a.L1 = dv.L1; a.a.chunk = hg.chunk; a.a.S = dv.S; a.a.Sint = dv.Sint;
@@ -1760,7 +1763,8 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         b.a.disp[0] = j.disp_l; b.a.disp[1] = j.disp_r;
         b.a.cost[0] = j.cost_l; b.a.cost[1] = j.cost_r;
         b.a.vol = j.vol; b.a.vol_view = j.vol_view;
-        b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
+        b.a.W = j.W; b.a.H = j.H; b.a.D = dv.dmin + j.D; b.a.dmin = dv.dmin;
+        b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
         b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
         set_wait(h, b.a);
@@ -1811,7 +1815,7 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
     std::map<int, size_t> hsm, vsm;
     for (const Job &j : jobs) {
         if (!j.vsrc || pass >= j.L.npass) continue;
-        const int d0 = pass * j.L.dc, dc = std::min(j.L.dc, j.D - d0);
+        const int d0 = dv.dmin + pass * j.L.dc, dc = std::min(j.L.dc, dv.dmin + j.D - d0);
         const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
         const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
         const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
@@ -1834,7 +1838,8 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
             b.a.disp[v] = j.vdst;
         }
         b.a.mask = j.vsrc;
-        b.a.W = j.W; b.a.H = j.H; b.a.D = j.D; b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
+        b.a.W = j.W; b.a.H = j.H; b.a.D = dv.dmin + j.D; b.a.dmin = dv.dmin;
+        b.a.d0 = d0; b.a.dc = dc; b.a.dstride = j.L.dstride;
         b.a.first = pass == 0; b.a.last = pass == j.L.npass - 1;
         b.a.status = h->d_status; b.a.L1 = dv.L1; b.a.chunk = vg.chunk; b.a.seglog = vg.seglog; b.a.S = dv.S;
         set_wait(h, b.a);
@@ -2009,6 +2014,7 @@ dco_status dco_params_default(dco_params *p)
     p->vote_iters = 0;
     p->smooth_arms = 0;
     p->agg_order = 0;
+    p->d_min = 0;
     return DCO_OK;
 }
 
@@ -2074,7 +2080,7 @@ size_t dco_stereo_workspace_bytes(int W, int H, int D, const dco_params *pin)
     dco_params p;
     if (pin) p = *pin;
     else dco_params_default(&p);
-    if (!params_valid(p) || !dims_valid(W, H, D)) return 0;
+    if (!params_valid(p) || !dims_valid(W, H, D, p.d_min)) return 0;
     return make_layout(W, H, D, p).total;
 }
 
@@ -2083,7 +2089,7 @@ dco_status dco_stereo_reserve(dco_stereo *h, int W, int H, int D, const dco_para
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     return ensure_ws(h, make_layout(W, H, D, p).total);
 }
 
@@ -2095,7 +2101,7 @@ dco_status dco_stereo_match_views(dco_stereo *h, const uint8_t *left, const uint
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!left || !right || !dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!left || !right || !dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     return run_match(h, left, right, W, H, D, p, disp_out, disp_left, disp_right, cost_left, cost_right,
                      nullptr, 0, (cudaStream_t)stream);
 }
@@ -2126,7 +2132,7 @@ dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host, const 
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!left_host || !right_host || !disp_host || !dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!left_host || !right_host || !disp_host || !dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     const size_t img = (size_t)W * H * 3, out = (size_t)W * H * 2;
     const size_t need = align_up(img) * 2 + align_up(out);
     cudaStream_t s = (cudaStream_t)stream;
@@ -2219,7 +2225,7 @@ dco_status dco_stereo_vote(dco_stereo *h, const uint8_t *rgb, const int16_t *dis
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!rgb || !disp_in || !disp_out || !dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!rgb || !disp_in || !disp_out || !dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Derived dv;
     derive(p, dv);
@@ -2256,7 +2262,7 @@ dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *r
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!left || !right || !depth_out || W < 2 || H < 2 || !dims_valid(W / 2, H / 2, D)) return DCO_EINVAL;
+    if (!left || !right || !depth_out || W < 2 || H < 2 || !dims_valid(W / 2, H / 2, D, p.d_min)) return DCO_EINVAL;
     if (!(f_px > 0.0) || !(baseline > 0.0) || !std::isfinite(f_px * baseline)) return DCO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int Wh = W / 2, Hh = H / 2;
@@ -2298,7 +2304,7 @@ dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint
     dco_params p;
     dco_status st = check_common(h, pin, p);
     if (st != DCO_OK) return st;
-    if (!left || !right || !vol_out || (view != 0 && view != 1) || !dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!left || !right || !vol_out || (view != 0 && view != 1) || !dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     return run_match(h, left, right, W, H, D, p, nullptr, nullptr, nullptr, nullptr, nullptr, vol_out, view,
                      (cudaStream_t)stream);
 }
@@ -2325,7 +2331,7 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
     if (n < 0 || (n > 0 && !descs)) return DCO_EINVAL;
     for (int i = 0; i < n; i++)
         if (!descs[i].left || !descs[i].right || !descs[i].disp_out ||
-            !dims_valid(descs[i].W, descs[i].H, descs[i].D) || descs[i].d_chunk < 0)
+            !dims_valid(descs[i].W, descs[i].H, descs[i].D, p.d_min) || descs[i].d_chunk < 0)
             return DCO_EINVAL;
     if (n == 0) return DCO_OK;
     std::vector<Job> jobs(n);
@@ -2476,7 +2482,7 @@ extern "C" dco_status dco_stereo_match_noalloc(const uint8_t *left, const uint8_
     dco_params p;
     if (pin) p = *pin;
     else dco_params_default(&p);
-    if (!params_valid(p) || !left || !right || !disp_out || !dims_valid(W, H, D)) return DCO_EINVAL;
+    if (!params_valid(p) || !left || !right || !disp_out || !dims_valid(W, H, D, p.d_min)) return DCO_EINVAL;
     p.d_chunk = 32;   // passes of 32 disparities keep the slices small
     Derived dv;
     derive(p, dv);

@@ -128,7 +128,8 @@ struct VArgs {
     int skip_copy;         // failure test: arm each tile's barrier but issue no copy
     int tm_rank;           // 4: tm as above; 3: dims (disparity, x, y), box 36 x 1 x 32 at (32 g, x, y)
     int vol_view;
-    int W, H, D;
+    int W, H, D;           // D: one past the largest disparity of the search (d_min + count)
+    int dmin;              // smallest disparity of the search
     int d0, dc, dstride;
     int first, last;       // first / last pass of the d range
     int L1;

@@ -278,7 +278,7 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
     else dco_params_default(&p);
     if (!params_valid(p)) return DCO_EINVAL;
     for (int i = 0; i < nstreams; i++)
-        if (!dims_valid(streams[i].W, streams[i].H, streams[i].D) || streams[i].d_chunk < 0) return DCO_EINVAL;
+        if (!dims_valid(streams[i].W, streams[i].H, streams[i].D, p.d_min) || streams[i].d_chunk < 0) return DCO_EINVAL;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DCO_EINVAL;
     dco_server *s = new (std::nothrow) dco_server();

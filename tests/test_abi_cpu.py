@@ -45,6 +45,17 @@ def test_host_only_entry_points(lib):
     assert lib.Stereo.workspace_bytes(1920, 1080, 256, p) < 2 * 1920 * 1080 * 256  # no full volume
     bad = lib.Params.default(arm_l1=41)
     assert lib.Stereo.workspace_bytes(64, 64, 16, bad) == 0
+    # Eq. 3's range [d_min, d_min + D - 1]: d_min >= 0, the largest disparity
+    # at most 255 and below W
+    ok = lib.Params.default(d_min=200)
+    assert p.d_min == 0
+    assert lib.Stereo.workspace_bytes(320, 64, 56, ok) > 0
+    assert lib.Stereo.workspace_bytes(320, 64, 57, ok) == 0            # d = 256
+    assert lib.Stereo.workspace_bytes(250, 64, 50, ok) > 0             # largest d = W - 1
+    assert lib.Stereo.workspace_bytes(249, 64, 50, ok) == 0            # d_min + D > W
+    assert lib.Stereo.workspace_bytes(64, 64, 16, lib.Params.default(d_min=-1)) == 0
+    # the slices hold D disparities, not d_min + D
+    assert lib.Stereo.workspace_bytes(320, 64, 56, ok) == lib.Stereo.workspace_bytes(320, 64, 56, p)
 
 
 def test_create_without_gpu_reports_an_error(lib):

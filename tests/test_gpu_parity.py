@@ -36,7 +36,7 @@ def oparams(bp):
                     gamma_l=float(bp.gamma_l), eps=float(bp.eps), census_w=bp.census_w,
                     census_h=bp.census_h, arm_l1=bp.arm_l1, arm_l2=bp.arm_l2, tau1=bp.tau1,
                     tau2=bp.tau2, lr_tol=bp.lr_tol, smooth_arms=bp.smooth_arms,
-                    agg_order=bp.agg_order)
+                    agg_order=bp.agg_order, d_min=bp.d_min)
 
 
 def run_views(env, left, right, D, bp=None):
@@ -279,6 +279,64 @@ def test_vh_order_config5_sampled_rows(env):
         parity.check_final(out[sl], ref, what + " final map", tally=tf)
     for t in (tl, tr, tf):
         t.close()
+
+
+# --------------------------------------------------------------- Eq. 3 range [d_min, d_max]
+@pytest.mark.parametrize("W,H,dmin,D,over", [(160, 96, 16, 48, {}), (200, 80, 5, 37, dict(d_chunk=32)),
+                                             (160, 96, 3, 29, dict(agg_order=1)), (320, 64, 200, 56, {}),
+                                             (96, 40, 40, 2, {}), (130, 70, 9, 70, dict(d_chunk=33))])
+def test_d_min_search(env, W, H, dmin, D, over):
+    # passes start at d_min (a ragged last pass where D is not a multiple of
+    # the pass width), maps hold absolute disparities, the largest range
+    # reaches d = 255 (the padded candidate rows)
+    torch, binding, st = env
+    s = scenes.plane_scene(W, H, dmin + D, 4, seed=scenes.seed_for(1, 400 + dmin + D),
+                           drange=(dmin + min(2, D - 1), dmin + max(min(2, D - 1), D - 3)), noise_sigma=2.0)
+    bp = binding.Params.default(d_min=dmin, **over)
+    n, out, dl, dr = full_check(env, s.left, s.right, D, bp, label=f"{W}x{H} d in [{dmin}, {dmin + D - 1}]")
+    for m in (dl, dr):
+        assert ((m >= dmin) & (m < dmin + D)).all()
+
+
+def test_d_min_cost_volume(env):
+    torch, binding, st = env
+    s = scenes.plane_scene(128, 64, 40, 3, seed=scenes.seed_for(1, 410), drange=(12, 36))
+    for view in (0, 1):
+        for order in (0, 1):
+            ref = O.match(s.left, s.right, 30, O.Params(d_min=10, agg_order=order), volume=True)
+            got = st.cost_volume(dev(torch, s.left), dev(torch, s.right), 30, view,
+                                 binding.Params.default(d_min=10, agg_order=order)).cpu().numpy()
+            parity.check_volume(got, ref.vol_r if view else ref.vol_l, f"volume view {view} order {order}, d_min 10")
+
+
+def test_d_min_vote(env):
+    # Eq. 4 over [d_min, d_max]: values below d_min neither vote nor survive
+    torch, binding, st = env
+    rng = np.random.default_rng(41)
+    s = scenes.plane_scene(150, 90, 60, 5, seed=scenes.seed_for(1, 420), drange=(22, 58))
+    d = np.clip(np.rint(s.disp), 0, 59).astype(np.int16)
+    u = rng.random(d.shape)
+    d[u < 0.15] = rng.integers(0, 60, int((u < 0.15).sum()))
+    d[(u >= 0.15) & (u < 0.25)] = -1
+    for dmin, D, it in ((20, 40, 2), (7, 33, 1)):
+        got = st.vote(dev(torch, s.left), dev(torch, d), D,
+                      binding.Params.default(d_min=dmin, vote_iters=it)).cpu().numpy()
+        st.sync_status()
+        assert np.array_equal(got, O.vote(d, O.arms(s.left), D, it, d_min=dmin))
+
+
+def test_d_min_batch_equals_single(env):
+    torch, binding, st = env
+    bp = binding.Params.default(d_min=12)
+    sc = [scenes.plane_scene(w, h, 12 + D, 3, seed=scenes.seed_for(1, 430 + w), drange=(14, 10 + D))
+          for (w, h, D) in ((160, 96, 40), (97, 61, 20), (256, 40, 64))]
+    pairs = [(dev(torch, x.left), dev(torch, x.right), x.D - 12, torch.empty((x.left.shape[0], x.left.shape[1]),
+                                                                              dtype=torch.int16, device="cuda"))
+             for x in sc]
+    st.match_batch(pairs, bp)
+    torch.cuda.synchronize()
+    for (l, r, D, o) in pairs:
+        assert np.array_equal(o.cpu().numpy(), st.match(l, r, D, bp).cpu().numpy())
 
 
 def _scenes_in_pool(config, items):

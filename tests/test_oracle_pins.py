@@ -420,17 +420,17 @@ def random_arms(rng, H, W, reach=3):
     return a
 
 
-def vote_bruteforce(disp, arm, D, iters):
+def vote_bruteforce(disp, arm, D, iters, d_min=0):
     """Eq. 4 written from the definition: the region as a set of coordinates
     (union over q on p's vertical arm of q's horizontal segment), a Python
-    dictionary of counts, max count with the smallest d."""
+    dictionary of counts, max count with the smallest d; d in [d_min, d_min + D)."""
     H, W = disp.shape
     cur = disp.astype(int).copy()
     for _ in range(iters):
         nxt = cur.copy()
         for y in range(H):
             for x in range(W):
-                if not 0 <= cur[y, x] < D:
+                if not d_min <= cur[y, x] < d_min + D:
                     nxt[y, x] = -1
                     continue
                 region = set()
@@ -440,7 +440,7 @@ def vote_bruteforce(disp, arm, D, iters):
                 counts = {}
                 for (xx, yy) in region:
                     v = cur[yy, xx]
-                    if 0 <= v < D:
+                    if d_min <= v < d_min + D:
                         counts[v] = counts.get(v, 0) + 1
                 top = max(counts.values())
                 nxt[y, x] = min(v for v, c in counts.items() if c == top)
@@ -504,6 +504,18 @@ def test_vote_matches_bruteforce():
         a = random_arms(rng, H, W)
         for k in (1, 2, 3):
             assert np.array_equal(O.vote(d, a, D, k), vote_bruteforce(d, a, D, k)), (H, W, D, k)
+
+
+def test_vote_with_d_min_matches_bruteforce():
+    # Eq. 4's range [d_min, d_max]: values below d_min are invalid like -1
+    rng = np.random.default_rng(14)
+    for H, W, D, dmin in ((5, 7, 6, 3), (8, 6, 4, 9), (1, 9, 5, 1)):
+        d = rng.integers(-1, dmin + D + 1, (H, W)).astype(np.int16)
+        a = random_arms(rng, H, W)
+        for k in (1, 2):
+            got = O.vote(d, a, D, k, d_min=dmin)
+            assert np.array_equal(got, vote_bruteforce(d, a, D, k, d_min=dmin)), (H, W, D, dmin, k)
+            assert ((got == -1) | ((got >= dmin) & (got < dmin + D))).all()
 
 
 def test_vote_iterations_compose():
@@ -779,3 +791,29 @@ def test_kernel_precision_decision_catches_a_planted_cost_error():
     bent = np.argmin(r.vol_l + 0.02 * np.arange(s.D)[:, None, None], axis=0).astype(np.int16)
     near = (r.second_l - r.best_l) <= 1e-4 * r.best_l + 1e-6
     assert ((bent != r.disp_l) & ~near).any()
+
+
+# ----------------------------------------------------------------- Eq. 3 range [d_min, d_max]
+@pytest.mark.parametrize("order", [0, 1])
+def test_d_min_search_is_the_sub_range_of_the_full_search(order):
+    # Eqs. 2-3 with d in [k, k + D): the aggregated costs are planes k .. k + D - 1
+    # of the search from 0 (Eq. 2 does not depend on the range), the decision
+    # the first argmin over those planes only, the checked map the LR check of
+    # the two absolute maps
+    s = scenes.plane_scene(48, 20, 24, 3, seed=21, drange=(6, 20), noise_sigma=2.0)
+    k, D = 5, 14
+    full = O.match(s.left, s.right, k + D, O.Params(agg_order=order), volume=True)
+    sub = O.match(s.left, s.right, D, O.Params(agg_order=order, d_min=k), volume=True, quantized=True)
+    for v, (fv, sv, sd, sb) in enumerate(((full.vol_l, sub.vol_l, sub.disp_l, sub.best_l),
+                                          (full.vol_r, sub.vol_r, sub.disp_r, sub.best_r))):
+        np.testing.assert_array_equal(sv, fv[k:])
+        assert np.array_equal(sd, k + np.argmin(fv[k:], axis=0)), v
+        np.testing.assert_array_equal(sb, fv[k:].min(axis=0))
+        assert (sd >= k).all() and (sd < k + D).all()
+    assert np.array_equal(sub.disp, O.lr_check(sub.disp_l, sub.disp_r, P.lr_tol))
+    assert (sub.qdisp_l >= k).all() and (sub.qdisp_r < k + D).all()
+    # a range that holds the whole truth gives the same map as the full search
+    # wherever the full search's decision lies inside it
+    inside = (full.disp_l >= k) & (full.disp_l < k + D)
+    assert inside.mean() > 0.8
+    assert np.array_equal(sub.disp_l[inside], full.disp_l[inside])
