@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--d-chunk", type=int, default=0, help="fixed pass width instead of the autotuner's")
+    ap.add_argument("--tile", default="", help="fixed tile d_chunk,h_chunk,v_chunk instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 3 batch and config 4 serving runs")
     ap.add_argument("--extras", default="all",
                     help="comma list of the extra measurements to run (vote_config2, depth_1280x720, "
@@ -208,8 +209,14 @@ def own_arm(args):
     R = Rh.to(dev)
     out = torch.empty((H, W), dtype=torch.int16, device=dev)
     st = binding.Stereo(local_rank)
-    dchunk = args.d_chunk if args.d_chunk > 0 else 0 if args.no_tune else tune.tune_d_chunk(st, L, R, D)
-    p = binding.Params.default(d_chunk=dchunk)
+    if args.tile:
+        tile = binding.Tile.of([int(v) for v in args.tile.split(",")])
+    elif args.d_chunk > 0 or args.no_tune:
+        tile = binding.Tile(args.d_chunk)
+    else:
+        tile = tune.tune_tiles(st, L, R, D)
+    dchunk = tile.d_chunk
+    p = tile.apply(binding.Params.default())
     npass = -(-D // (dchunk or D))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -330,14 +337,14 @@ def own_arm(args):
             frames4 = render_frames(scenes.STREAMS_CONFIG4, 16, processes=4)
             d4 = tune.tune_batch(st, scenes.STREAMS_CONFIG4, device=local_rank)
             extras["serve_config4"] = serve_config4_native(torch, binding, st, local_rank, frames=frames4,
-                                                           d_chunks=d4)
+                                                           tiles=d4)
             extras["serve_config4_5x_rate"] = serve_config4_native(torch, binding, st, local_rank, time_scale=5.0,
-                                                                   frames=frames4, d_chunks=d4)
+                                                                   frames=frames4, tiles=d4)
             extras["serve_config4_saturation"] = serve_saturation(torch, local_rank, frames4, d4)
             # the same replay through the Python serving loop, with the plain
             # single calls of each size and the served == alone check
             extras["serve_config4_python_loop"] = serve_config4(torch, binding, st, local_rank, frames=frames4,
-                                                                d_chunks=d4)
+                                                                tiles=d4)
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -351,7 +358,8 @@ def own_arm(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 cost, u32 fixed-point aggregation",
             "data": "synthetic (seeded plane scene; the paper's INDEMIND / Middlebury data are not available)",
-            "config": dict(CONFIG, d_chunk=dc, passes=npass, parallelism=f"replicas x{world}"),
+            "config": dict(CONFIG, d_chunk=dc, h_chunk=tile.h_chunk, v_chunk=tile.v_chunk, passes=npass,
+                           parallelism=f"replicas x{world}"),
             "frames_per_s": 1e3 * args.steps * world / total_ms,
             "latency_ms": {"p50": statistics.median(lat), "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * W * H * 3,
@@ -632,7 +640,8 @@ def _timed(torch, dev, flush, fn, reps):
 def batch_config3(torch, binding, st, flush, dev, reps: int = 10):
     """32 pairs of uneven size: one batched pass (CUDA-graph replay) against
     the same pairs matched one call at a time, both with the library's
-    automatic pass width and with each shape's pass width from the autotuner;
+    automatic tiles and with each shape's tile (pass width, blocks of the two
+    1-D passes) from the autotuner;
     L2 flushed before each."""
     from paper_2203_02300_gb300 import scenes, tune
     from paper_2203_02300_gb300.batch import BatchGraph
@@ -644,10 +653,10 @@ def batch_config3(torch, binding, st, flush, dev, reps: int = 10):
     units = sum(s.W * s.H * s.D for s in sc)
     tuned = tune.tune_batch(st, shapes, device=dev.index or 0)
     g = BatchGraph(binding.Stereo(dev.index or 0), shapes, device=dev.index or 0)
-    gt = BatchGraph(binding.Stereo(dev.index or 0), shapes, device=dev.index or 0, d_chunks=tuned)
+    gt = BatchGraph(binding.Stereo(dev.index or 0), shapes, device=dev.index or 0, tiles=tuned)
     g.load(L, R)
     gt.load(L, R)
-    pt = [binding.Params.default(d_chunk=dc) for dc in tuned]
+    pt = [t.apply(binding.Params.default()) for t in tuned]
 
     def sequential():
         for l, r, s, o in zip(L, R, sc, outs):
@@ -663,12 +672,12 @@ def batch_config3(torch, binding, st, flush, dev, reps: int = 10):
     t_bat_t = _timed(torch, dev, flush, gt.replay, reps)
     same = all(torch.equal(a, b) and torch.equal(a, c) for a, b, c in zip(outs, g.out, gt.out))
     sizes = sorted(set(shapes))
-    tiles = {f"{w}x{h} D={d}": tuned[shapes.index((w, h, d))] for w, h, d in sizes}
+    tiles = {f"{w}x{h} D={d}": list(tuned[shapes.index((w, h, d))]) for w, h, d in sizes}
     return {"pairs": len(sc), "sizes": [f"{w}x{h} D={d}" for w, h, d in sizes], "evals": units,
             "batched_graph_ms": t_bat, "batched_evals_per_s": units / (t_bat * 1e-3),
             "sequential_ms": t_seq, "sequential_evals_per_s": units / (t_seq * 1e-3),
             "speedup": t_seq / t_bat,
-            "tuned_pass_width": tiles,
+            "tuned_tiles_d_h_v": tiles,
             "tuned_batched_graph_ms": t_bat_t, "tuned_batched_evals_per_s": units / (t_bat_t * 1e-3),
             "tuned_sequential_ms": t_seq_t, "tuned_sequential_evals_per_s": units / (t_seq_t * 1e-3),
             "tuned_batch_over_default_sequential": t_seq / t_bat_t,
@@ -697,7 +706,7 @@ def batch_config5(torch, binding, flush, dev, reps: int = 3, budget: int = 1_500
             "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3)}
 
 
-def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, d_chunks=None):
+def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None):
     """Config 4 through the library's native serving runtime (dco_server_*:
     scheduler and completion threads in C++, maps copied straight into
     pinned output buffers); the same replay and comparison as serve_config4."""
@@ -705,16 +714,16 @@ def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.
     from paper_2203_02300_gb300 import scenes
     from paper_2203_02300_gb300.serve import run_config4_native
     stats, _, frames = run_config4_native(frames_per_stream=300, rate_hz=30.0, device=device, time_scale=time_scale,
-                                          frames=frames, d_chunks=d_chunks)
+                                          frames=frames, tiles=tiles)
     stats = dict(stats)
     stats["per_stream"] = {f"{W}x{H} D={D} (stream {k})": v for (W, H, D), (k, v) in
                            zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
     return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
             "frames_per_stream": 300, "unique_frames_per_stream": len(frames[0]), "rate_hz": 30 * time_scale,
-            "pass_width": d_chunks, **stats}
+            "tiles_d_h_v": [list(t) for t in tiles] if tiles else None, **stats}
 
 
-def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, d_chunks=None):
+def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None):
     """4 camera streams, 300 frames each (cycled from 16 rendered ones per
     stream, planes moving 0-3 px per frame), Poisson arrivals at 30 Hz (real
     time): continuous batching over two lanes; p50/p99 from arrival to map on
@@ -724,12 +733,12 @@ def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, fram
     from paper_2203_02300_gb300 import scenes
     from paper_2203_02300_gb300.serve import run_config4
     stats, outs, frames = run_config4(frames_per_stream=300, rate_hz=30.0, device=device,
-                                      time_scale=time_scale, frames=frames, server_kw={"d_chunks": d_chunks})
+                                      time_scale=time_scale, frames=frames, server_kw={"tiles": tiles})
     plain = {}
     for i, (W, H, D) in enumerate(scenes.STREAMS_CONFIG4):
         l, r = frames[i][0]
         outh = np.empty((H, W), np.int16)
-        p = binding.Params.default(d_chunk=d_chunks[i] if d_chunks else 0)
+        p = binding.Tile.of(tiles[i] if tiles else None).apply(binding.Params.default())
         for _ in range(3):
             st.match_host(l.numpy(), r.numpy(), D, p, out=outh)
         ts = []
@@ -744,18 +753,19 @@ def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, fram
                            zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
     return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
             "frames_per_stream": 300, "unique_frames_per_stream": len(frames[0]), "rate_hz": 30 * time_scale,
-            "pass_width": d_chunks, **stats, "plain_single_call": plain}
+            "tiles_d_h_v": [list(t) for t in tiles] if tiles else None, **stats, "plain_single_call": plain}
 
 
-def serve_saturation(torch, device: int, frames, d_chunks, seconds: float = 3.0, native: bool = True):
+def serve_saturation(torch, device: int, frames, tiles, seconds: float = 3.0, native: bool = True):
     """Closed loop: every stream keeps its three slots busy for `seconds`;
     the serving throughput ceiling and the latency at that load."""
     from paper_2203_02300_gb300.serve import run_saturation, run_saturation_native
     if native:
-        st = run_saturation_native(seconds, device=device, frames=frames, d_chunks=d_chunks)
+        st = run_saturation_native(seconds, device=device, frames=frames, tiles=tiles)
     else:
-        st = run_saturation(seconds, device=device, frames=frames, server_kw={"d_chunks": d_chunks})
-    return {"seconds": seconds, "slots_per_stream": 3, "pass_width": d_chunks, **st}
+        st = run_saturation(seconds, device=device, frames=frames, server_kw={"tiles": tiles})
+    return {"seconds": seconds, "slots_per_stream": 3, "tiles_d_h_v": [list(t) for t in tiles] if tiles else None,
+            **st}
 
 
 # ------------------------------------------------------- oracle timing

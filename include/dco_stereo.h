@@ -111,6 +111,8 @@ typedef struct {
     int smooth_arms; /* 1: smooth cross-support window (Sect. 4.1), see above; 0 = raw arms */
     int agg_order; /* 0: horizontal then vertical sums (Eq. 2); 1: vertical then horizontal */
     int d_min; /* smallest disparity searched (Eq. 3's d_min): d in [d_min, d_min + D - 1]; 0 */
+    int h_chunk; /* tile: scan positions per block of the first 1-D pass (0 = automatic); see below */
+    int v_chunk; /* tile: output positions per block of the second 1-D pass (0 = automatic) */
 } dco_params;
 
 /* Fill *p with the defaults above.  DCO_EINVAL if p is NULL. */
@@ -154,6 +156,14 @@ dco_status dco_stereo_reserve(dco_stereo *h, int W, int H, int D, const dco_para
  * left, right: device, W*H*3 bytes.  disp_out: device, W*H int16.
  * The disparity range is processed in passes of p->d_chunk disparities
  * (automatic when 0) so the workspace holds slices, never the volume.
+ * Tile shapes (they change the speed, never the result): the first 1-D
+ * pass (rows for agg_order 0, columns for 1) splits each line into blocks
+ * of p->h_chunk outputs (0: whole lines up to 1024 positions, else 512;
+ * otherwise 32 <= h_chunk, capped at 1024 - 2 arm_l1 below the line); the second
+ * pass splits each line into balanced blocks of at most p->v_chunk outputs
+ * (0: whole lines up to 512 positions, else blocks of at most 432; otherwise
+ * 32 <= v_chunk, capped at 512 - 2 arm_l1).  Each block reads arm_l1
+ * positions of halo on both sides.
  * p = NULL uses the defaults.
  */
 dco_status dco_stereo_match(dco_stereo *h, const uint8_t *left, const uint8_t *right,
@@ -306,6 +316,7 @@ typedef struct {
     int W, H, D;
     int16_t *disp_out;
     int d_chunk;
+    int h_chunk, v_chunk; /* this pair's tile shapes (0: the call's p->h_chunk / v_chunk) */
 } dco_pair_desc;
 
 /*
@@ -410,12 +421,14 @@ dco_status dco_stereo_noalloc_status(dco_stream stream);
  * dco_stereo_match_batch (the whole path of dco_stereo_match for every
  * frame) and copies each map straight into the caller's buffer.  Frames that
  * arrive while other batches are on the device are admitted as slots and
- * lanes free up, so their work overlaps on the device.  A completion thread
- * retires each lane's batches on their events and wakes the callers.
+ * lanes free up, so their work overlaps on the device.  One completion
+ * thread per lane retires that lane's batches on their events and wakes the
+ * callers, so a short batch is never held up behind a longer one on another
+ * lane.
  * Results equal dco_stereo_match on each frame alone (bit for bit).
  *
- * dco_server_create: streams[nstreams] the stream shapes (d_chunk 0: the
- *   params' pass width); lanes 1..16; slots_per_stream >= 1 (frames of one
+ * dco_server_create: streams[nstreams] the stream shapes (d_chunk, h_chunk,
+ *   v_chunk 0: the params' pass width and tiles); lanes 1..16; slots_per_stream >= 1 (frames of one
  *   stream in flight at once); max_batch >= 1 frames per batch;
  *   budget_bytes the device workspace of all lanes together (0: every
  *   stream's frame in every lane's batch).  The server allocates its slots
@@ -441,6 +454,7 @@ typedef struct dco_server dco_server;
 typedef struct {
     int W, H, D;
     int d_chunk;
+    int h_chunk, v_chunk; /* tile shapes of the stream's frames (0: the params') */
 } dco_stream_desc;
 typedef struct {
     double arrival_s;  /* submit time, steady clock seconds */

@@ -2,8 +2,8 @@
 
 `dco_stereo_match_batch` runs each stage of the path as one launch over all
 pairs (up to 64 pairs per launch, descriptors in the kernel parameters).
-`BatchGraph` fixes a set of pair shapes (and, optionally, each pair's pass
-width from the autotuner), reserves the workspace, warms the
+`BatchGraph` fixes a set of pair shapes (and, optionally, each pair's tile
+choice from the autotuner: pass width and blocks), reserves the workspace, warms the
 library up (tables, shared-memory opt-ins), captures the batched call on a
 stream into a CUDA graph, and replays it for new inputs copied into its
 static device buffers.  Only buffer management and graph bookkeeping live
@@ -13,13 +13,13 @@ from __future__ import annotations
 
 from typing import Optional, Sequence
 
-from .binding import Params, Stereo
+from .binding import Params, Stereo, Tile
 
 
 class BatchGraph:
     def __init__(self, stereo: Stereo, shapes: Sequence[tuple[int, int, int]],
                  params: Optional[Params] = None, device: int = 0,
-                 d_chunks: Optional[Sequence[int]] = None):
+                 tiles: Optional[Sequence] = None):
         import torch
         self.st = stereo
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
@@ -31,10 +31,10 @@ class BatchGraph:
         self.stream = torch.cuda.Stream(self.dev)
         for t in self.left + self.right:
             t.zero_()
-        # per-pair pass widths (e.g. tune.tune_batch); 0 = the call's parameters
-        self.d_chunks = [int(v) for v in (d_chunks or [0] * len(self.shapes))]
-        pairs = [(l, r, D, o, dc) for l, r, (_, _, D), o, dc
-                 in zip(self.left, self.right, self.shapes, self.out, self.d_chunks)]
+        # per-pair tiles (e.g. tune.tune_batch); 0 fields = the call's parameters
+        self.tiles = [Tile.of(v) for v in (tiles or [None] * len(self.shapes))]
+        pairs = [(l, r, D, o, t) for l, r, (_, _, D), o, t
+                 in zip(self.left, self.right, self.shapes, self.out, self.tiles)]
         self._pairs = pairs
         # warm-up outside capture: workspace, tables, shared-memory opt-ins
         with torch.cuda.stream(self.stream):

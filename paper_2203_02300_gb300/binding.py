@@ -12,7 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
-from typing import Optional, Sequence
+from typing import NamedTuple, Optional, Sequence
 
 import numpy as np
 
@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
                 ("eps", c_float), ("census_w", c_int), ("census_h", c_int), ("arm_l1", c_int),
                 ("arm_l2", c_int), ("tau1", c_int), ("tau2", c_int), ("lr_tol", c_int),
                 ("d_chunk", c_int), ("vote_iters", c_int), ("smooth_arms", c_int),
-                ("agg_order", c_int), ("d_min", c_int)]
+                ("agg_order", c_int), ("d_min", c_int), ("h_chunk", c_int), ("v_chunk", c_int)]
 
     @classmethod
     def default(cls, **over) -> "Params":
@@ -57,13 +57,39 @@ class DenseParams(ctypes.Structure):
         return p
 
 
+class Tile(NamedTuple):
+    """Per-shape tile choice: the pass width (disparities per pass) and the
+    blocks of the two 1-D passes (dco_params.d_chunk, h_chunk, v_chunk);
+    0 = the call's parameters."""
+    d_chunk: int = 0
+    h_chunk: int = 0
+    v_chunk: int = 0
+
+    @classmethod
+    def of(cls, v) -> "Tile":
+        """A Tile from None, a pass width alone or a (d, h, v) sequence."""
+        if v is None:
+            return cls()
+        if isinstance(v, (int, np.integer)):
+            return cls(int(v))
+        return cls(*(int(x) for x in v))
+
+    def apply(self, p: "Params") -> "Params":
+        """p with this tile's nonzero fields set."""
+        for k, v in zip(self._fields, self):
+            if v:
+                setattr(p, k, v)
+        return p
+
+
 class PairDesc(ctypes.Structure):
     _fields_ = [("left", c_void_p), ("right", c_void_p), ("W", c_int), ("H", c_int), ("D", c_int),
-                ("disp_out", c_void_p), ("d_chunk", c_int)]
+                ("disp_out", c_void_p), ("d_chunk", c_int), ("h_chunk", c_int), ("v_chunk", c_int)]
 
 
 class StreamDesc(ctypes.Structure):
-    _fields_ = [("W", c_int), ("H", c_int), ("D", c_int), ("d_chunk", c_int)]
+    _fields_ = [("W", c_int), ("H", c_int), ("D", c_int), ("d_chunk", c_int), ("h_chunk", c_int),
+                ("v_chunk", c_int)]
 
 
 class RequestTimes(ctypes.Structure):
@@ -287,15 +313,16 @@ class Stereo:
 
     def match_batch(self, pairs: Sequence, params: Optional[Params] = None, stream=None):
         """pairs: sequence of (left, right, D, out) device tensors, or
-        (left, right, D, out, d_chunk) with the pair's own pass width."""
+        (left, right, D, out, tile) with the pair's own pass width (an int)
+        or Tile (pass width and blocks)."""
         arr = (PairDesc * len(pairs))()
         for i, pr in enumerate(pairs):
             l, r, D, o = pr[:4]
-            dchunk = int(pr[4]) if len(pr) > 4 and pr[4] else 0
+            t = Tile.of(pr[4] if len(pr) > 4 else None)
             W, H = _rgb_dims(l)
             _expect(f"pair {i} right", r, l.shape, "uint8", l)
             _expect(f"pair {i} out", o, (H, W), "int16", l)
-            arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o), dchunk)
+            arr[i] = PairDesc(_ptr(l), _ptr(r), W, H, D, _ptr(o), *t)
         _check(lib().dco_stereo_match_batch(self._h, arr, len(pairs),
                                             ctypes.byref(params) if params else None, _stream(stream)),
                self._h)
@@ -454,10 +481,10 @@ class NativeServer:
     in the output buffer and returns the request's times."""
 
     def __init__(self, shapes, device: int = 0, lanes: int = 2, slots_per_stream: int = 3, max_batch: int = 16,
-                 budget_bytes: int = 0, params: Optional[Params] = None, d_chunks=None):
+                 budget_bytes: int = 0, params: Optional[Params] = None, tiles=None):
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
-        dcs = [int(v) for v in (d_chunks or [0] * len(self.shapes))]
-        arr = (StreamDesc * len(self.shapes))(*[StreamDesc(W, H, D, dc) for (W, H, D), dc in zip(self.shapes, dcs)])
+        ts = [Tile.of(v) for v in (tiles or [None] * len(self.shapes))]
+        arr = (StreamDesc * len(self.shapes))(*[StreamDesc(W, H, D, *t) for (W, H, D), t in zip(self.shapes, ts)])
         self._s = c_void_p()
         self._keep = {}
         _check(lib().dco_server_create(ctypes.byref(self._s), device, arr, len(self.shapes), lanes, slots_per_stream,

@@ -1140,6 +1140,7 @@ struct Derived {
     float S;
     int order;   // aggregation order: 0 horizontal then vertical, 1 vertical then horizontal
     int dmin;    // smallest disparity of the search
+    int hchunk, vchunk;   // tile shapes of the two 1-D passes (0: automatic)
 };
 
 struct Layout {
@@ -1162,8 +1163,13 @@ bool derive(const dco_params &p, Derived &d)
     d.S = (float)s;
     d.order = p.agg_order;
     d.dmin = p.d_min;
+    d.hchunk = p.h_chunk;
+    d.vchunk = p.v_chunk;
     return true;
 }
+
+// a tile shape: 0 (automatic) or 32 .. 16384 positions
+bool tile_valid(int c) { return c == 0 || (c >= 32 && c <= 16384); }
 
 bool params_valid(const dco_params &p)
 {
@@ -1177,6 +1183,7 @@ bool params_valid(const dco_params &p)
     if (p.smooth_arms != 0 && p.smooth_arms != 1) return false;
     if (p.agg_order != 0 && p.agg_order != 1) return false;
     if (p.d_min < 0 || p.d_min > 255) return false;
+    if (!tile_valid(p.h_chunk) || !tile_valid(p.v_chunk)) return false;
     return true;
 }
 
@@ -1232,10 +1239,21 @@ struct HGeom {
 // the other aggregation order: k_vcost walks columns (one chunk of rows per
 // block while it fits 32 warps of 32 rows), k_vagg<.., kRow> rows (the scan
 // range along x at most 512 columns, like k_vagg's rows)
-HGeom vcost_geom(int W, int H, int dc, int L1)
+// Output positions per block of a first-pass line of n positions: the whole
+// line up to kHMaxLen, else 512 (want = 0); otherwise `want`, capped so that
+// a block's prefix range (chunk + 2 L1 halo) stays within kHMaxLen.
+int first_pass_chunk(int n, int L1, int want)
+{
+    if (want <= 0) return n <= kHMaxLen ? n : 512;
+    int c = std::min(want, n);
+    if (c < n || n > kHMaxLen) c = std::min(c, kHMaxLen - 2 * L1);
+    return c;
+}
+
+HGeom vcost_geom(int W, int H, int dc, int L1, int want)
 {
     HGeom g{};
-    g.chunk = H <= kHMaxLen ? H : 512;
+    g.chunk = first_pass_chunk(H, L1, want);
     const int len = std::min(H, g.chunk + 2 * L1);
     g.nw = (len + kHSegCost - 1) / kHSegCost;
     g.smem = CSmem(len, g.chunk, g.nw).total;
@@ -1243,10 +1261,10 @@ HGeom vcost_geom(int W, int H, int dc, int L1)
     return g;
 }
 
-HGeom hagg_geom(int W, int H, int dc, int L1)
+HGeom hagg_geom(int W, int H, int dc, int L1, int want)
 {
     HGeom g{};
-    g.chunk = W <= kHMaxLen ? W : 512;
+    g.chunk = first_pass_chunk(W, L1, want);
     const int len = std::min(W, g.chunk + 2 * L1);
     g.nw = (len + kHSegCost - 1) / kHSegCost;
     g.smem = HSmem(len, g.chunk, g.nw).total;
@@ -1262,11 +1280,20 @@ struct VGeom {
     dim3 grid;
 };
 
-VGeom vagg_geom(int W, int H, int L1)
+VGeom vagg_geom(int W, int H, int L1, int want)
 {
     VGeom g{};
-    // at most 16 warps of 32 rows: the prefix range (chunk + 2*L1) <= 512
-    const int nchunks = H <= 512 ? 1 : (H + (512 - 2 * kMaxL1) - 1) / (512 - 2 * kMaxL1);
+    // at most 16 warps of 32 rows: the prefix range (chunk + 2*L1) <= 512;
+    // balanced chunks of at most `want` rows (automatic: whole columns up
+    // to 512 rows, else at most 512 - 2 kMaxL1)
+    int nchunks;
+    if (want <= 0) {
+        nchunks = H <= 512 ? 1 : (H + (512 - 2 * kMaxL1) - 1) / (512 - 2 * kMaxL1);
+    } else {
+        int c = std::min(want, H);
+        if (c < H || H > 512) c = std::min(c, 512 - 2 * L1);
+        nchunks = (H + c - 1) / c;
+    }
     g.chunk = (H + nchunks - 1) / nchunks;
     const int len = std::min(H, g.chunk + 2 * L1);
     g.seglog = 5;   // 32 rows per warp, one output row per lane
@@ -1569,6 +1596,7 @@ struct Job {
     int vol_view = 0;
     uchar4 *arms0 = nullptr;   // stage entry point: arms of image 0 go here
     int dchunk = 0;                  // this pair's pass width (0: the call's parameters)
+    int hchunk = 0, vchunk = 0;      // this pair's tile shapes (0: the call's parameters)
     const int16_t *vsrc = nullptr;   // Eq. 4 round: map voted on (null: no vote)
     int16_t *vdst = nullptr;         //   and the map written
     Layout L{};
@@ -1737,8 +1765,9 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
     for (const Job &j : jobs) {
         if (pass >= j.L.npass) continue;
         const int d0 = dv.dmin + pass * j.L.dc, dc = std::min(j.L.dc, dv.dmin + j.D - d0);
-        const HGeom hg = vh ? vcost_geom(j.W, j.H, dc, dv.L1) : hagg_geom(j.W, j.H, dc, dv.L1);
-        const VGeom vg = vh ? vagg_geom(j.H, j.W, dv.L1) : vagg_geom(j.W, j.H, dv.L1);
+        const int hw = j.hchunk > 0 ? j.hchunk : dv.hchunk, vw = j.vchunk > 0 ? j.vchunk : dv.vchunk;
+        const HGeom hg = vh ? vcost_geom(j.W, j.H, dc, dv.L1, hw) : hagg_geom(j.W, j.H, dc, dv.L1, hw);
+        const VGeom vg = vh ? vagg_geom(j.H, j.W, dv.L1, vw) : vagg_geom(j.W, j.H, dv.L1, vw);
         hsm[hg.nw] = std::max(hsm[hg.nw], hg.smem);
         vsm[vg.nw] = std::max(vsm[vg.nw], vg.smem);
         Item<HArgs> a{};
@@ -1816,8 +1845,9 @@ dco_status launch_vote_pass(dco_stereo *h, const Derived &dv, const std::vector<
     for (const Job &j : jobs) {
         if (!j.vsrc || pass >= j.L.npass) continue;
         const int d0 = dv.dmin + pass * j.L.dc, dc = std::min(j.L.dc, dv.dmin + j.D - d0);
-        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1);
-        const VGeom vg = vagg_geom(j.W, j.H, dv.L1);
+        const int hw = j.hchunk > 0 ? j.hchunk : dv.hchunk, vw = j.vchunk > 0 ? j.vchunk : dv.vchunk;
+        const HGeom hg = hagg_geom(j.W, j.H, dc, dv.L1, hw);
+        const VGeom vg = vagg_geom(j.W, j.H, dv.L1, vw);
         const int hlen = std::min(j.W, hg.chunk + 2 * dv.L1), vlen = std::min(j.H, vg.chunk + 2 * dv.L1);
         const int hnw = (hlen + kHSeg - 1) / kHSeg;   // the vote pass walks 64-column segments
         hsm[hnw] = std::max(hsm[hnw], (size_t)HVSmem(hlen, hg.chunk, hnw).total);
@@ -2015,6 +2045,8 @@ dco_status dco_params_default(dco_params *p)
     p->smooth_arms = 0;
     p->agg_order = 0;
     p->d_min = 0;
+    p->h_chunk = 0;
+    p->v_chunk = 0;
     return DCO_OK;
 }
 
@@ -2331,7 +2363,8 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
     if (n < 0 || (n > 0 && !descs)) return DCO_EINVAL;
     for (int i = 0; i < n; i++)
         if (!descs[i].left || !descs[i].right || !descs[i].disp_out ||
-            !dims_valid(descs[i].W, descs[i].H, descs[i].D, p.d_min) || descs[i].d_chunk < 0)
+            !dims_valid(descs[i].W, descs[i].H, descs[i].D, p.d_min) || descs[i].d_chunk < 0 ||
+            !tile_valid(descs[i].h_chunk) || !tile_valid(descs[i].v_chunk))
             return DCO_EINVAL;
     if (n == 0) return DCO_OK;
     std::vector<Job> jobs(n);
@@ -2340,6 +2373,8 @@ dco_status dco_stereo_match_batch(dco_stereo *h, const dco_pair_desc *descs, int
         jobs[i].W = descs[i].W; jobs[i].H = descs[i].H; jobs[i].D = descs[i].D;
         jobs[i].out = descs[i].disp_out;
         jobs[i].dchunk = descs[i].d_chunk;
+        jobs[i].hchunk = descs[i].h_chunk;
+        jobs[i].vchunk = descs[i].v_chunk;
     }
     return run_jobs(h, p, jobs, (cudaStream_t)stream);
 }

@@ -4,8 +4,10 @@
 // the frame's stream, the batch's workspace within a lane's share of the
 // memory budget), runs each batch on a free lane (a handle with its own
 // workspace and CUDA stream: copies in, dco_stereo_match_batch, map copied
-// straight into the caller's buffer), and a completion thread retires the
-// lanes' batches in order on their events, waking the callers.  Frames that
+// straight into the caller's buffer), and one completion thread per lane
+// retires that lane's batches on their events, waking the callers (a lane's
+// batches finish in order on its stream; a short batch on one lane is never
+// held up behind a long one on another).  Frames that
 // arrive while other batches are on the device are admitted as slots and a
 // lane free up, so their work overlaps on the device.  Included at the end
 // of dco_stereo.cu; uses only the public C ABI for the matching itself.
@@ -40,16 +42,17 @@ struct SrvSlot {
     bool busy = false;
 };
 
-struct SrvLane {
-    dco_stereo *h = nullptr;
-    cudaStream_t stream = nullptr;
-    bool busy = false;
-};
-
 struct SrvBatch {
     int lane = 0;
     cudaEvent_t start = nullptr, end = nullptr;
     std::vector<SrvReq *> reqs;
+};
+
+struct SrvLane {
+    dco_stereo *h = nullptr;
+    cudaStream_t stream = nullptr;
+    bool busy = false;
+    std::deque<SrvBatch> inflight;   // launched, not yet retired (at most one: the lane is busy meanwhile)
 };
 
 } // namespace
@@ -66,12 +69,12 @@ struct dco_server {
     std::mutex mu;
     std::condition_variable sched_cv, done_cv, wait_cv;
     std::deque<SrvReq *> pending;
-    std::deque<SrvBatch> inflight;
     std::unordered_map<unsigned long long, SrvReq *> reqs;
     unsigned long long next_ticket = 1;
     bool stop = false;
     bool sched_done = false;                 // the scheduler has drained the pending frames and left
-    std::thread sched, compl_;
+    std::thread sched;
+    std::vector<std::thread> compl_;   // one completion thread per lane
     std::vector<cudaEvent_t> event_pool;
     unsigned long long batches = 0, frames_batched = 0;
     size_t max_batch_bytes = 0;
@@ -147,7 +150,7 @@ dco_status srv_launch(dco_server *s, SrvLane &ln, const std::vector<SrvReq *> &b
         if (cudaMemcpyAsync(sl.left, r->left, img, cudaMemcpyHostToDevice, ln.stream) != cudaSuccess ||
             cudaMemcpyAsync(sl.right, r->right, img, cudaMemcpyHostToDevice, ln.stream) != cudaSuccess)
             return DCO_ECUDA;
-        descs[k] = dco_pair_desc{sl.left, sl.right, d.W, d.H, d.D, sl.out, d.d_chunk};
+        descs[k] = dco_pair_desc{sl.left, sl.right, d.W, d.H, d.D, sl.out, d.d_chunk, d.h_chunk, d.v_chunk};
     }
     dco_status st = dco_stereo_match_batch(ln.h, descs.data(), (int)descs.size(), &s->params, ln.stream);
     if (st != DCO_OK) return st;
@@ -206,22 +209,23 @@ void srv_schedule(dco_server *s)
         }
         s->batches++;
         s->frames_batched += batch.size();
-        s->inflight.push_back(b);
+        ln.inflight.push_back(b);
         s->done_cv.notify_all();
     }
     s->sched_done = true;
     s->done_cv.notify_all();
 }
 
-void srv_complete(dco_server *s)
+void srv_complete(dco_server *s, int lane)
 {
     cudaSetDevice(s->device);
+    SrvLane &ln = s->lanes[lane];
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->done_cv.wait(lk, [&] { return !s->inflight.empty() || s->sched_done; });
-        if (s->inflight.empty()) break;   // the scheduler has left and every batch is retired
-        SrvBatch b = s->inflight.front();
-        s->inflight.pop_front();
+        s->done_cv.wait(lk, [&] { return !ln.inflight.empty() || s->sched_done; });
+        if (ln.inflight.empty()) break;   // the scheduler has left and this lane's batches are retired
+        SrvBatch b = ln.inflight.front();
+        ln.inflight.pop_front();
         lk.unlock();
         const cudaError_t e = cudaEventSynchronize(b.end);
         const double t = now_s();
@@ -278,7 +282,9 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
     else dco_params_default(&p);
     if (!params_valid(p)) return DCO_EINVAL;
     for (int i = 0; i < nstreams; i++)
-        if (!dims_valid(streams[i].W, streams[i].H, streams[i].D, p.d_min) || streams[i].d_chunk < 0) return DCO_EINVAL;
+        if (!dims_valid(streams[i].W, streams[i].H, streams[i].D, p.d_min) || streams[i].d_chunk < 0 ||
+            !tile_valid(streams[i].h_chunk) || !tile_valid(streams[i].v_chunk))
+            return DCO_EINVAL;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DCO_EINVAL;
     dco_server *s = new (std::nothrow) dco_server();
@@ -331,7 +337,7 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
             for (auto &sl : s->slots[i]) {
                 const dco_stream_desc &d = s->streams[i];
                 if (used + s->ws[i] <= s->lane_budget && (int)warm.size() < max_batch) {
-                    warm.push_back(dco_pair_desc{sl.left, sl.right, d.W, d.H, d.D, sl.out, d.d_chunk});
+                    warm.push_back(dco_pair_desc{sl.left, sl.right, d.W, d.H, d.D, sl.out, d.d_chunk, d.h_chunk, d.v_chunk});
                     used += s->ws[i];
                 }
             }
@@ -348,7 +354,7 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
         return st;
     }
     s->sched = std::thread(srv_schedule, s);
-    s->compl_ = std::thread(srv_complete, s);
+    for (int k = 0; k < (int)s->lanes.size(); k++) s->compl_.emplace_back(srv_complete, s, k);
     *out = s;
     return DCO_OK;
 }
@@ -423,7 +429,7 @@ void dco_server_destroy(dco_server *s)
     }
     s->sched_cv.notify_all();
     s->sched.join();   // admits and launches every pending frame first
-    s->compl_.join();  // then every batch in flight is retired
+    for (auto &t : s->compl_) t.join();   // then every batch in flight is retired
     srv_free(s);
 }
 

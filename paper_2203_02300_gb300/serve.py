@@ -31,7 +31,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from .binding import Params, Stereo
+from .binding import Params, Stereo, Tile
 
 
 @dataclasses.dataclass
@@ -66,22 +66,20 @@ class Server:
     def __init__(self, shapes: Sequence[tuple[int, int, int]], budget_bytes: Optional[int] = None,
                  lanes: int = 2, slots_per_stream: int = 3, max_batch: int = 16,
                  params: Optional[Params] = None, device: int = 0,
-                 d_chunks: Optional[Sequence[int]] = None):
+                 tiles: Optional[Sequence] = None):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         self.params = params
         self.max_batch = max_batch
-        # each stream's pass width (e.g. tune.tune_batch); 0 = the params' own
-        self.d_chunks = [int(v) for v in (d_chunks or [0] * len(self.shapes))]
+        # each stream's tiles (e.g. tune.tune_batch); 0 fields = the params' own
+        self.tiles = [Tile.of(v) for v in (tiles or [None] * len(self.shapes))]
 
         def ws_of(s):
             W, H, D = self.shapes[s]
             p = Params.default(**{f: getattr(params, f) for f, _ in Params._fields_}) if params else Params.default()
-            if self.d_chunks[s]:
-                p.d_chunk = self.d_chunks[s]
-            return Stereo.workspace_bytes(W, H, D, p)
+            return Stereo.workspace_bytes(W, H, D, self.tiles[s].apply(p))
         ws = [ws_of(s) for s in range(len(self.shapes))]
         if budget_bytes is None:
             budget_bytes = lanes * sum(ws)   # every stream can be in every lane's batch
@@ -98,7 +96,7 @@ class Server:
         for s, (W, H, D) in enumerate(self.shapes):
             for sl in self.slots[s]:
                 if used + ws[s] <= self.lane_budget and len(warm) < max_batch:
-                    warm.append((sl.left, sl.right, D, sl.out, self.d_chunks[s]))
+                    warm.append((sl.left, sl.right, D, sl.out, self.tiles[s]))
                     used += ws[s]
         for sl_list in self.slots:
             for sl in sl_list:
@@ -218,7 +216,7 @@ class Server:
                         sl = self.slots[r.stream][r.slot]
                         sl.left.copy_(r.left, non_blocking=True)
                         sl.right.copy_(r.right, non_blocking=True)
-                        pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out, self.d_chunks[r.stream]))
+                        pairs.append((sl.left, sl.right, self.shapes[r.stream][2], sl.out, self.tiles[r.stream]))
                     t_launch = time.perf_counter()
                     ev0 = torch.cuda.Event(enable_timing=True)
                     ev0.record(lane.stream)
@@ -391,7 +389,7 @@ def _native_stats(records, nstreams: int, counters: dict) -> dict:
 
 
 def run_config4_native(frames_per_stream: int = 300, rate_hz: float = 30.0, time_scale: float = 1.0,
-                       unique_frames: int = 6, shapes=None, device: int = 0, frames=None, d_chunks=None,
+                       unique_frames: int = 6, shapes=None, device: int = 0, frames=None, tiles=None,
                        keep_outputs: bool = False, server_kw=None):
     """Config 4 replayed through the library's native serving runtime
     (dco_server_*): Poisson arrivals per stream, each frame's map copied by
@@ -418,7 +416,7 @@ def run_config4_native(frames_per_stream: int = 300, rate_hz: float = 30.0, time
         W, H, _ = shapes[i]
         return torch.empty((H, W), dtype=torch.int16).pin_memory().numpy()
     outs = {} if keep_outputs else {(i, j): out_buf(i, j) for i in range(len(shapes)) for j in range(ring)}
-    srv = NativeServer(shapes, device=device, d_chunks=d_chunks, **kw)
+    srv = NativeServer(shapes, device=device, tiles=tiles, **kw)
     tickets = [collections.deque() for _ in shapes]   # per stream, oldest first
     records = []
 
@@ -453,7 +451,7 @@ def run_config4_native(frames_per_stream: int = 300, rate_hz: float = 30.0, time
 
 
 def run_saturation_native(duration_s: float = 3.0, shapes=None, unique_frames: int = 4, device: int = 0,
-                          frames=None, d_chunks=None, server_kw=None):
+                          frames=None, tiles=None, server_kw=None):
     """Closed loop through the native runtime: every stream keeps its slots
     busy (a new frame as soon as one of the stream completes) for
     `duration_s` seconds."""
@@ -465,7 +463,7 @@ def run_saturation_native(duration_s: float = 3.0, shapes=None, unique_frames: i
     unique_frames = len(frames[0])
     kw = dict(server_kw or {})
     depth = kw.get("slots_per_stream", 3)
-    srv = NativeServer(shapes, device=device, d_chunks=d_chunks, **kw)
+    srv = NativeServer(shapes, device=device, tiles=tiles, **kw)
     bufs = {(i, j): torch.empty((shapes[i][1], shapes[i][0]), dtype=torch.int16).pin_memory().numpy()
             for i in range(len(shapes)) for j in range(depth)}
     records = []

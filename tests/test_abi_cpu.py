@@ -54,6 +54,12 @@ def test_host_only_entry_points(lib):
     assert lib.Stereo.workspace_bytes(250, 64, 50, ok) > 0             # largest d = W - 1
     assert lib.Stereo.workspace_bytes(249, 64, 50, ok) == 0            # d_min + D > W
     assert lib.Stereo.workspace_bytes(64, 64, 16, lib.Params.default(d_min=-1)) == 0
+    # tile shapes: 0 (automatic) or 32 .. 16384 positions; they do not
+    # change the workspace
+    for h, v, ok_ in ((0, 0, True), (32, 32, True), (16384, 96, True), (16, 0, False), (0, 31, False),
+                      (-1, 0, False), (0, 16385, False)):
+        ws_t = lib.Stereo.workspace_bytes(640, 480, 64, lib.Params.default(h_chunk=h, v_chunk=v))
+        assert (ws_t == ws) if ok_ else (ws_t == 0), (h, v)
     # the slices hold D disparities, not d_min + D
     assert lib.Stereo.workspace_bytes(320, 64, 56, ok) == lib.Stereo.workspace_bytes(320, 64, 56, p)
 

@@ -201,6 +201,26 @@ def test_tuner_picks_a_candidate_and_caches_it(env, tmp_path, monkeypatch):
     monkeypatch.setenv("DCO_TUNE_CACHE", str(tmp_path / "tiles.json"))
     W, H, D = 320, 240, 96
     won = tune.tune_shape(st, W, H, D, reps=2)
-    assert won in tune.candidates(W, H, D)
+    assert won.d_chunk in tune.candidates(W, H, D)
+    assert won.h_chunk in tune.first_pass_candidates(W) and won.v_chunk in tune.second_pass_candidates(H)
     assert tune.lookup(W, H, D, torch.cuda.get_device_name(0)) == won
     assert tune.tune_batch(st, [(W, H, D), (W, H, D)]) == [won, won]
+    # the tuned tile changes the speed, not the maps
+    s = scenes.plane_scene(W, H, D, 4, seed=scenes.seed_for(3, 90), drange=(2, 90))
+    l, r = _dev(torch, s.left), _dev(torch, s.right)
+    assert torch.equal(st.match(l, r, D, won.apply(binding.Params.default())), st.match(l, r, D))
+
+
+def test_batch_with_per_pair_tiles(env, config3):
+    # dco_pair_desc h_chunk / v_chunk: each pair its own blocks of the two
+    # 1-D passes; results equal the pair alone with automatic tiles
+    torch, binding, st = env
+    sub = config3[:8]
+    tiles = [binding.Tile(0, 64, 0), binding.Tile(32, 0, 96), binding.Tile(0, 160, 120), binding.Tile(64, 96, 64),
+             binding.Tile(), binding.Tile(0, 128, 200), binding.Tile(96, 320, 32), binding.Tile(0, 0, 50)]
+    pairs = [(_dev(torch, s.left), _dev(torch, s.right), s.D,
+              torch.empty((s.H, s.W), dtype=torch.int16, device="cuda"), t) for s, t in zip(sub, tiles)]
+    st.match_batch(pairs)
+    torch.cuda.synchronize()
+    for s, pr in zip(sub, pairs):
+        assert np.array_equal(pr[3].cpu().numpy(), _single(env, s))

@@ -33,3 +33,26 @@ def test_buffers_must_match_shape_type_layout_and_device():
     meta = torch.empty((4, 6), dtype=torch.int16, device="meta")
     with pytest.raises(ValueError):
         B._expect("out", meta, (4, 6), "int16", out)                  # device
+
+
+def test_tile_candidates_follow_the_block_limits():
+    # the autotuner only proposes blocks the library accepts: 0 (automatic)
+    # or at least 32 positions, a first-pass block with its 2 x arm_l1 halo
+    # within 1024 prefix positions unless it is a whole line of <= 1024, a
+    # second-pass block within 512 - 2 x arm_l1 unless it is a whole column
+    # of <= 512; each candidate a different block count
+    from paper_2203_02300_gb300 import tune
+    from paper_2203_02300_gb300.binding import Tile
+    for L1 in (34, 40, 3):
+        for n in (33, 97, 160, 320, 480, 640, 720, 1080, 1280, 1920, 4000):
+            hs = tune.first_pass_candidates(n, L1)
+            vs = tune.second_pass_candidates(n, L1)
+            assert hs[0] == 0 and vs[0] == 0
+            for c in hs[1:]:
+                assert 32 <= c < n and c + 2 * L1 <= 1024, (n, L1, c)
+            for c in vs[1:]:
+                assert 32 <= c <= n and (c == n <= 512 or c <= 512 - 2 * L1), (n, L1, c)
+            counts = [-(-n // c) for c in vs[1:]]
+            assert len(set(counts)) == len(counts)
+            assert len(set(hs)) == len(hs)
+    assert Tile.of(None) == Tile() and Tile.of(64) == Tile(64, 0, 0) and Tile.of((32, 96, 120)) == Tile(32, 96, 120)

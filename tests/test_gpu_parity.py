@@ -281,6 +281,37 @@ def test_vh_order_config5_sampled_rows(env):
         t.close()
 
 
+# --------------------------------------------------------------- tile shapes
+@pytest.mark.parametrize("order", [0, 1])
+def test_tile_shapes_change_nothing(env, order):
+    # blocks of the two 1-D passes (h_chunk, v_chunk) from 32 positions to
+    # whole lines, with and without narrow passes: every map and cost equals
+    # the automatic tiles' bit for bit, and the oracle's parity rule holds
+    torch, binding, st = env
+    s = scenes.config_scene(2)
+    auto = run_views(env, s.left, s.right, s.D, binding.Params.default(agg_order=order))
+    for d, h, v in ((0, 32, 0), (0, 0, 32), (0, 96, 100), (32, 320, 240), (0, 224, 160), (48, 600, 479),
+                    (0, 16384, 16384), (0, 1000, 0)):
+        got = run_views(env, s.left, s.right, s.D,
+                        binding.Params.default(agg_order=order, d_chunk=d, h_chunk=h, v_chunk=v))
+        for a, b in zip(got, auto):
+            assert np.array_equal(a, b), (d, h, v)
+    full_check(env, s.left, s.right, s.D, binding.Params.default(agg_order=order, h_chunk=96, v_chunk=100),
+               label=f"config 2 order {order} tiles 96 x 100")
+
+
+def test_tile_shapes_config5_rows(env):
+    # 1920 x 1080: first-pass blocks of 288 and 640 columns, second-pass
+    # blocks of 135 and 270 rows against the automatic (512, 360)
+    torch, binding, st = env
+    s = scenes.config_scene(5)
+    L, R = dev(torch, s.left), dev(torch, s.right)
+    auto = st.match(L, R, s.D).cpu().numpy()
+    for h, v in ((288, 135), (640, 270)):
+        got = st.match(L, R, s.D, binding.Params.default(h_chunk=h, v_chunk=v)).cpu().numpy()
+        assert np.array_equal(got, auto), (h, v)
+
+
 # --------------------------------------------------------------- Eq. 3 range [d_min, d_max]
 @pytest.mark.parametrize("W,H,dmin,D,over", [(160, 96, 16, 48, {}), (200, 80, 5, 37, dict(d_chunk=32)),
                                              (160, 96, 3, 29, dict(agg_order=1)), (320, 64, 200, 56, {}),

@@ -52,6 +52,20 @@ def test_vote_equals_oracle(env, W, H, D, chunk, iters):
     assert (got[(d < 0) | (d >= D)] == -1).all()
 
 
+def test_vote_with_tiles_equals_oracle(env):
+    # the vote's passes use the call's blocks of the two 1-D passes too
+    torch, binding, st = env
+    rng = np.random.default_rng(17)
+    s = scenes.plane_scene(200, 150, 48, 5, seed=scenes.seed_for(1, 330), drange=(1, 46))
+    d = _noisy_map(rng, s, 48)
+    want = O.vote(d, O.arms(s.left), 48, 2)
+    for h, v in ((64, 48), (32, 32), (128, 0), (0, 100)):
+        p = binding.Params.default(vote_iters=2, h_chunk=h, v_chunk=v)
+        got = st.vote(_dev(torch, s.left), _dev(torch, d), 48, p).cpu().numpy()
+        st.sync_status()
+        assert np.array_equal(got, want), (h, v)
+
+
 def test_vote_removes_outliers(env):
     torch, binding, st = env
     rng = np.random.default_rng(7)
