@@ -336,10 +336,14 @@ def own_arm(args):
             from paper_2203_02300_gb300.serve import render_frames
             frames4 = render_frames(scenes.STREAMS_CONFIG4, 16, processes=4)
             d4 = tune.tune_batch(st, scenes.STREAMS_CONFIG4, device=local_rank)
+            # the smaller streams latency-critical (shortest job first), and
+            # the same replay with every stream in plain arrival order
             extras["serve_config4"] = serve_config4_native(torch, binding, st, local_rank, frames=frames4,
-                                                           tiles=d4)
+                                                           tiles=d4, priorities="smaller")
+            extras["serve_config4_fifo"] = serve_config4_native(torch, binding, st, local_rank, frames=frames4,
+                                                                tiles=d4)
             extras["serve_config4_5x_rate"] = serve_config4_native(torch, binding, st, local_rank, time_scale=5.0,
-                                                                   frames=frames4, tiles=d4)
+                                                                   frames=frames4, tiles=d4, priorities="smaller")
             extras["serve_config4_saturation"] = serve_saturation(torch, local_rank, frames4, d4)
             # the same replay through the Python serving loop, with the plain
             # single calls of each size and the served == alone check
@@ -706,21 +710,26 @@ def batch_config5(torch, binding, flush, dev, reps: int = 3, budget: int = 1_500
             "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3)}
 
 
-def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None):
+def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None,
+                         priorities=None):
     """Config 4 through the library's native serving runtime (dco_server_*:
     scheduler and completion threads in C++, maps copied straight into
     pinned output buffers); the same replay and comparison as serve_config4."""
     import numpy as np
     from paper_2203_02300_gb300 import scenes
     from paper_2203_02300_gb300.serve import run_config4_native
+    clocks = Clocks(device if torch.cuda.device_count() > 1 else 0)
+    clocks.start()
     stats, _, frames = run_config4_native(frames_per_stream=300, rate_hz=30.0, device=device, time_scale=time_scale,
-                                          frames=frames, tiles=tiles)
-    stats = dict(stats)
+                                          frames=frames, tiles=tiles,
+                                          server_kw={"priorities": priorities} if priorities else None)
+    stats = dict(stats, clocks=clocks.stop())
     stats["per_stream"] = {f"{W}x{H} D={D} (stream {k})": v for (W, H, D), (k, v) in
                            zip(scenes.STREAMS_CONFIG4, sorted(stats.get("per_stream", {}).items()))}
     return {"streams": [f"{W}x{H} D={D}" for W, H, D in scenes.STREAMS_CONFIG4],
             "frames_per_stream": 300, "unique_frames_per_stream": len(frames[0]), "rate_hz": 30 * time_scale,
-            "tiles_d_h_v": [list(t) for t in tiles] if tiles else None, **stats}
+            "tiles_d_h_v": [list(t) for t in tiles] if tiles else None,
+            "latency_critical_streams": priorities or "none", **stats}
 
 
 def serve_config4(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None):

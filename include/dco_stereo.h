@@ -424,7 +424,11 @@ dco_status dco_stereo_noalloc_status(dco_stream stream);
  * lanes free up, so their work overlaps on the device.  One completion
  * thread per lane retires that lane's batches on their events and wakes the
  * callers, so a short batch is never held up behind a longer one on another
- * lane.
+ * lane.  Streams marked latency-critical (dco_stream_desc.priority = 1, e.g.
+ * the smaller frame sizes: shortest job first) are admitted first, batched
+ * only with each other, and run on the lane's CUDA stream of the greatest
+ * priority, so the block scheduler gives their kernels the SMs ahead of a
+ * larger frame's blocks already waiting on the device.
  * Results equal dco_stereo_match on each frame alone (bit for bit).
  *
  * dco_server_create: streams[nstreams] the stream shapes (d_chunk, h_chunk,
@@ -455,6 +459,7 @@ typedef struct {
     int W, H, D;
     int d_chunk;
     int h_chunk, v_chunk; /* tile shapes of the stream's frames (0: the params') */
+    int priority;         /* 1: latency-critical stream (see above); 0: normal */
 } dco_stream_desc;
 typedef struct {
     double arrival_s;  /* submit time, steady clock seconds */

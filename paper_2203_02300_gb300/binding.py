@@ -89,7 +89,7 @@ class PairDesc(ctypes.Structure):
 
 class StreamDesc(ctypes.Structure):
     _fields_ = [("W", c_int), ("H", c_int), ("D", c_int), ("d_chunk", c_int), ("h_chunk", c_int),
-                ("v_chunk", c_int)]
+                ("v_chunk", c_int), ("priority", c_int)]
 
 
 class RequestTimes(ctypes.Structure):
@@ -481,10 +481,18 @@ class NativeServer:
     in the output buffer and returns the request's times."""
 
     def __init__(self, shapes, device: int = 0, lanes: int = 2, slots_per_stream: int = 3, max_batch: int = 16,
-                 budget_bytes: int = 0, params: Optional[Params] = None, tiles=None):
+                 budget_bytes: int = 0, params: Optional[Params] = None, tiles=None, priorities=None):
+        """priorities: per stream 1 = latency-critical (admitted first, run on
+        high-priority CUDA streams), 0 = normal; "smaller" marks every
+        stream whose frames are smaller (W x H x D) than the largest."""
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
         ts = [Tile.of(v) for v in (tiles or [None] * len(self.shapes))]
-        arr = (StreamDesc * len(self.shapes))(*[StreamDesc(W, H, D, *t) for (W, H, D), t in zip(self.shapes, ts)])
+        if priorities == "smaller":
+            big = max(W * H * D for W, H, D in self.shapes)
+            priorities = [int(W * H * D < big) for W, H, D in self.shapes]
+        pr = [int(v) for v in (priorities or [0] * len(self.shapes))]
+        arr = (StreamDesc * len(self.shapes))(*[StreamDesc(W, H, D, *t, q)
+                                                for (W, H, D), t, q in zip(self.shapes, ts, pr)])
         self._s = c_void_p()
         self._keep = {}
         _check(lib().dco_server_create(ctypes.byref(self._s), device, arr, len(self.shapes), lanes, slots_per_stream,

@@ -44,13 +44,15 @@ struct SrvSlot {
 
 struct SrvBatch {
     int lane = 0;
+    bool hi = false;   // frames of latency-critical streams: the lane's high-priority stream
     cudaEvent_t start = nullptr, end = nullptr;
     std::vector<SrvReq *> reqs;
 };
 
 struct SrvLane {
     dco_stereo *h = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // batches of normal streams
+    cudaStream_t stream_hi = nullptr;   // batches of latency-critical streams (greatest priority)
     bool busy = false;
     std::deque<SrvBatch> inflight;   // launched, not yet retired (at most one: the lane is busy meanwhile)
 };
@@ -104,11 +106,28 @@ cudaEvent_t srv_event(dco_server *s)
 // Admit pending requests in arrival order while the batch has room, the
 // request's stream has a free slot and the lane's share of the budget holds
 // its workspace; the ones left behind keep their order.  Caller holds mu.
-std::vector<SrvReq *> srv_form_batch(dco_server *s)
+// a pending frame of stream `st` can be admitted now (a free slot)
+bool srv_slot_free(const dco_server *s, int st)
+{
+    for (const SrvSlot &sl : s->slots[st])
+        if (!sl.busy) return true;
+    return false;
+}
+
+// The next batch: frames of latency-critical streams first (a batch holds
+// frames of one class only), in arrival order within the class, while the
+// frame's stream has a free slot and the batch fits the lane's budget.
+std::vector<SrvReq *> srv_form_batch(dco_server *s, bool &hi)
 {
     std::vector<SrvReq *> batch;
     std::deque<SrvReq *> skipped;
     size_t used = 0;
+    hi = false;
+    for (const SrvReq *r : s->pending)
+        if (s->streams[r->stream].priority && srv_slot_free(s, r->stream)) {
+            hi = true;
+            break;
+        }
     while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
         SrvReq *r = s->pending.front();
         s->pending.pop_front();
@@ -118,7 +137,7 @@ std::vector<SrvReq *> srv_form_batch(dco_server *s)
                 si = (int)k;
                 break;
             }
-        if (si < 0 || used + s->ws[r->stream] > s->lane_budget) {
+        if (si < 0 || (s->streams[r->stream].priority != 0) != hi || used + s->ws[r->stream] > s->lane_budget) {
             skipped.push_back(r);
             continue;
         }
@@ -135,32 +154,34 @@ std::vector<SrvReq *> srv_form_batch(dco_server *s)
     return batch;
 }
 
-// copies in, the batched match, the maps out, on the lane's stream
+// copies in, the batched match, the maps out, on the lane's stream of the
+// batch's class
 dco_status srv_launch(dco_server *s, SrvLane &ln, const std::vector<SrvReq *> &batch, SrvBatch &b)
 {
     cudaSetDevice(s->device);
     (void)cudaGetLastError();
     std::vector<dco_pair_desc> descs(batch.size());
-    if (cudaEventRecord(b.start, ln.stream) != cudaSuccess) return DCO_ECUDA;
+    const cudaStream_t cs = b.hi ? ln.stream_hi : ln.stream;
+    if (cudaEventRecord(b.start, cs) != cudaSuccess) return DCO_ECUDA;
     for (size_t k = 0; k < batch.size(); k++) {
         const SrvReq *r = batch[k];
         const dco_stream_desc &d = s->streams[r->stream];
         const SrvSlot &sl = s->slots[r->stream][r->slot];
         const size_t img = (size_t)d.W * d.H * 3;
-        if (cudaMemcpyAsync(sl.left, r->left, img, cudaMemcpyHostToDevice, ln.stream) != cudaSuccess ||
-            cudaMemcpyAsync(sl.right, r->right, img, cudaMemcpyHostToDevice, ln.stream) != cudaSuccess)
+        if (cudaMemcpyAsync(sl.left, r->left, img, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+            cudaMemcpyAsync(sl.right, r->right, img, cudaMemcpyHostToDevice, cs) != cudaSuccess)
             return DCO_ECUDA;
         descs[k] = dco_pair_desc{sl.left, sl.right, d.W, d.H, d.D, sl.out, d.d_chunk, d.h_chunk, d.v_chunk};
     }
-    dco_status st = dco_stereo_match_batch(ln.h, descs.data(), (int)descs.size(), &s->params, ln.stream);
+    dco_status st = dco_stereo_match_batch(ln.h, descs.data(), (int)descs.size(), &s->params, cs);
     if (st != DCO_OK) return st;
     for (const SrvReq *r : batch) {
         const dco_stream_desc &d = s->streams[r->stream];
         const SrvSlot &sl = s->slots[r->stream][r->slot];
-        if (cudaMemcpyAsync(r->out, sl.out, (size_t)d.W * d.H * 2, cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess)
+        if (cudaMemcpyAsync(r->out, sl.out, (size_t)d.W * d.H * 2, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
             return DCO_ECUDA;
     }
-    return cudaEventRecord(b.end, ln.stream) == cudaSuccess ? DCO_OK : DCO_ECUDA;
+    return cudaEventRecord(b.end, cs) == cudaSuccess ? DCO_OK : DCO_ECUDA;
 }
 
 void srv_schedule(dco_server *s)
@@ -175,7 +196,8 @@ void srv_schedule(dco_server *s)
             return (s->stop && s->pending.empty()) || (!s->pending.empty() && li >= 0);
         });
         if (s->pending.empty()) break;   // stopping, nothing left to admit
-        std::vector<SrvReq *> batch = srv_form_batch(s);
+        bool hi = false;
+        std::vector<SrvReq *> batch = srv_form_batch(s, hi);
         if (batch.empty()) {   // every pending frame waits for a slot: wait for a completion
             s->sched_cv.wait_for(lk, std::chrono::milliseconds(1));
             continue;
@@ -184,6 +206,7 @@ void srv_schedule(dco_server *s)
         ln.busy = true;
         SrvBatch b;
         b.lane = li;
+        b.hi = hi;
         b.start = srv_event(s);
         b.end = srv_event(s);
         b.reqs = batch;
@@ -193,7 +216,7 @@ void srv_schedule(dco_server *s)
         const dco_status st = srv_launch(s, ln, batch, b);
         lk.lock();
         if (st != DCO_OK) {   // this batch's requests fail; the server keeps serving
-            cudaStreamSynchronize(ln.stream);
+            cudaStreamSynchronize(hi ? ln.stream_hi : ln.stream);
             (void)cudaGetLastError();
             for (SrvReq *r : batch) {
                 r->status = st;
@@ -252,8 +275,10 @@ void srv_free(dco_server *s)
     cudaSetDevice(s->device);
     for (auto &ln : s->lanes) {
         if (ln.stream) cudaStreamSynchronize(ln.stream);
+        if (ln.stream_hi) cudaStreamSynchronize(ln.stream_hi);
         dco_stereo_destroy(ln.h);
         if (ln.stream) cudaStreamDestroy(ln.stream);
+        if (ln.stream_hi) cudaStreamDestroy(ln.stream_hi);
     }
     for (auto &v : s->slots)
         for (auto &sl : v) {
@@ -283,7 +308,8 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
     if (!params_valid(p)) return DCO_EINVAL;
     for (int i = 0; i < nstreams; i++)
         if (!dims_valid(streams[i].W, streams[i].H, streams[i].D, p.d_min) || streams[i].d_chunk < 0 ||
-            !tile_valid(streams[i].h_chunk) || !tile_valid(streams[i].v_chunk))
+            !tile_valid(streams[i].h_chunk) || !tile_valid(streams[i].v_chunk) ||
+            (streams[i].priority != 0 && streams[i].priority != 1))
             return DCO_EINVAL;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DCO_EINVAL;
@@ -326,7 +352,11 @@ dco_status dco_server_create(dco_server **out, int device, const dco_stream_desc
     for (auto &ln : s->lanes) {
         if (st != DCO_OK) break;
         if ((st = dco_stereo_create(&ln.h, device, s->lane_budget)) != DCO_OK) break;
-        if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess) st = DCO_ECUDA;
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ln.stream, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ln.stream_hi, cudaStreamNonBlocking, greatest) != cudaSuccess)
+            st = DCO_ECUDA;
     }
     // warm every lane up with the largest batch admission allows, so its
     // workspace never grows (a synchronising reallocation) while serving

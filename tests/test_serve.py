@@ -154,3 +154,20 @@ def test_native_runtime_rejects_bad_requests(env):
     with _pt.raises(binding.DcoError) as e:   # a lane's share cannot hold one frame
         binding.NativeServer(SHAPES, budget_bytes=1000)
     assert e.value.code == binding.DCO_EBUDGET
+    for bad in (dict(priorities=[2] + [0] * (len(SHAPES) - 1)), dict(tiles=[(0, 16, 0)] * len(SHAPES))):
+        with _pt.raises(binding.DcoError) as e:
+            binding.NativeServer(SHAPES, **bad)
+        assert e.value.code == binding.DCO_EINVAL
+
+
+def test_native_runtime_with_latency_critical_streams_equals_alone(env):
+    # the smaller streams marked latency-critical: admitted first, batched
+    # only with each other, run on high-priority CUDA streams; every map
+    # still equals the frame matched alone
+    from paper_2203_02300_gb300.serve import run_config4_native
+    stats, outs, frames = run_config4_native(frames_per_stream=16, rate_hz=400.0, unique_frames=4, shapes=SHAPES,
+                                             keep_outputs=True, server_kw={"priorities": "smaller"})
+    alone = _alone(env, frames)
+    for (i, k), got in outs.items():
+        assert np.array_equal(got, alone[(i, k % 4)]), (i, k)
+    assert stats["frames"] == 16 * len(SHAPES)
