@@ -1025,6 +1025,38 @@ struct Batch {
     A p[N];
 };
 
+// Programmatic dependent launch: every batched kernel is launched with
+// programmatic stream serialization, so the launch of a kernel overlaps the
+// end of the previous one in the stream.  Before touching global memory a
+// block waits until the previous grids have completed and their writes are
+// visible.  No block triggers its dependents early: blocks of the next
+// kernel parked on free SMs while a multi-pass run's last waves drain made
+// those runs slower (1920x1080 in passes of 32: 5.12 against 4.31 ms);
+// with the trigger at grid exit the launch latency alone is hidden
+// (640x480 D=64: 165 -> 156 us per pair, 320x240 D=32: 46 -> 36.5 us).
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+// launch with programmatic stream serialization (the kernel calls pdl_enter
+// before any global memory access)
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <class A, int N>
 __device__ __forceinline__ int batch_pair(const Batch<A, N> &b, int flat, int &bx, int &by, int &bz)
 {
@@ -1045,6 +1077,7 @@ __device__ __forceinline__ int batch_pair(const Batch<A, N> &b, int flat, int &b
 template <int N, bool kMax>
 __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ Batch<SmoothArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     smooth_body<kMax>(b.p[i], bx * 256 + threadIdx.x, by);
@@ -1053,6 +1086,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ Batch<Sm
 template <int N>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Batch<PackArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     pack_body(b.p[i], bx * 256 + threadIdx.x, by);
@@ -1061,6 +1095,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Batch<Pack
 template <int CW, int CH, int N>
 __global__ void __launch_bounds__(kTX * kTY) k_prep(const __grid_constant__ Batch<PrepArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     prep_body<CW, CH>(b.p[i], bx, by, bz);
@@ -1070,6 +1105,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_prep(const __grid_constant__ Batc
 template <int N, bool kWide>
 __global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __grid_constant__ Batch<HArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     hagg_body(b.p[i], bx, by, bz);
@@ -1078,6 +1114,7 @@ __global__ void __launch_bounds__(kWide ? 1024 : kHNarrow * 32) k_hagg(const __g
 template <int N, bool kMax, bool kRow = false>
 __global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Batch<VArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     vagg_body<kMax, kRow>(b.p[i], bx, by, bz);
@@ -1086,6 +1123,7 @@ __global__ void __launch_bounds__(16 * 32, 2) k_vagg(const __grid_constant__ Bat
 template <int N>
 __global__ void __launch_bounds__(1024) k_vcost(const __grid_constant__ Batch<HArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     vcost_body(b.p[i], bx, by, bz);
@@ -1094,6 +1132,7 @@ __global__ void __launch_bounds__(1024) k_vcost(const __grid_constant__ Batch<HA
 template <int N>
 __global__ void __launch_bounds__(16 * 32) k_hvote(const __grid_constant__ Batch<HVArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     hvote_body(b.p[i], bx, by, bz);
@@ -1102,6 +1141,7 @@ __global__ void __launch_bounds__(16 * 32) k_hvote(const __grid_constant__ Batch
 template <int N>
 __global__ void __launch_bounds__(256) k_lr(const __grid_constant__ Batch<LrArgs, N> b)
 {
+    pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
     lr_body(b.p[i], (size_t)bx * 256 + threadIdx.x);
@@ -1559,8 +1599,8 @@ dco_status launch_group(dco_stereo *h, cudaStream_t s, const char *name, K kerne
         if (st != DCO_OK) return st;
     }
     ProfScope ps(h, s, name);
-    kernel<<<b.off[n], block, smem, s>>>(b);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(kernel, dim3((unsigned)b.off[n]), dim3((unsigned)block), smem, s, b);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         h->last_error = std::string(name) + " launch (" + std::to_string(n) + " pairs, " + std::to_string(b.off[n]) +
                         " blocks of " + std::to_string(block) + " threads, " + std::to_string(smem) +

@@ -100,6 +100,7 @@ __device__ __forceinline__ bool dn_reduce(float v0, float v1, const DnArgs &a, d
 // weights, diagonal, right-hand side, initial guess (the data where present)
 __global__ void __launch_bounds__(kDnBlock) k_dn_setup(const DnArgs a)
 {
+    pdl_enter();
     const unsigned n = (unsigned)a.W * a.H, W = (unsigned)a.W;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.sc->count = 0;
@@ -139,6 +140,7 @@ __device__ __forceinline__ float dn_apply(const DnArgs &a, const float *v, unsig
 // r = b - A x0, z = r / diag, partials of r.z and b.b
 __global__ void __launch_bounds__(kDnBlock) k_dn_init(const DnArgs a)
 {
+    pdl_enter();
     const unsigned n = (unsigned)a.W * a.H;
     float rz = 0.0f, bb = 0.0f;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_init(const DnArgs a)
 // p_new = z + beta p_old, Ap = A p_new (p_new of the neighbours formed on the fly)
 __global__ void __launch_bounds__(kDnBlock) k_dn_ap(const DnArgs a, int it)
 {
+    pdl_enter();
     if (a.sc->done) return;
     const unsigned n = (unsigned)a.W * a.H, W = (unsigned)a.W;
     const float *po = a.p[it & 1];
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_ap(const DnArgs a, int it)
 // x += alpha p, r -= alpha Ap, z = r / diag; partials of r.z and r.r
 __global__ void __launch_bounds__(kDnBlock) k_dn_upd(const DnArgs a, int it)
 {
+    pdl_enter();
     if (a.sc->done) return;
     const unsigned n = (unsigned)a.W * a.H;
     const float alpha = (float)a.sc->alpha;
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_upd(const DnArgs a, int it)
 // drifts from the true residual), z = r / diag; partials of r.z and r.r
 __global__ void __launch_bounds__(kDnBlock) k_dn_resid(const DnArgs a)
 {
+    pdl_enter();
     if (a.sc->done) return;
     const unsigned n = (unsigned)a.W * a.H, W = (unsigned)a.W;
     float rz = 0.0f, rr = 0.0f;
@@ -319,11 +324,11 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
     a.tol2 = (double)p.tol * p.tol;
     {
         ProfScope ps(h, s, "k_dn_setup");
-        k_dn_setup<<<nblk, kDnBlock, 0, s>>>(a);
+        launch_pdl(k_dn_setup, dim3(nblk), dim3(kDnBlock), 0, s, a);
     }
     {
         ProfScope ps(h, s, "k_dn_init");
-        k_dn_init<<<nblk, kDnBlock, 0, s>>>(a);
+        launch_pdl(k_dn_init, dim3(nblk), dim3(kDnBlock), 0, s, a);
     }
     DCO_CUDA(h, cudaGetLastError());
     // Iterations run in batches of kDnIters, each closed by the residual
@@ -338,16 +343,16 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
             const int it = it0 + k;
             {
                 ProfScope ps(h, q, prof ? "k_dn_ap" : nullptr);
-                k_dn_ap<<<nblk, kDnBlock, 0, q>>>(a, it);
+                launch_pdl(k_dn_ap, dim3(nblk), dim3(kDnBlock), 0, q, a, it);
             }
             {
                 ProfScope ps(h, q, prof ? "k_dn_upd" : nullptr);
-                k_dn_upd<<<nblk, kDnBlock, 0, q>>>(a, it);
+                launch_pdl(k_dn_upd, dim3(nblk), dim3(kDnBlock), 0, q, a, it);
             }
         }
         {
             ProfScope ps(h, q, prof ? "k_dn_resid" : nullptr);
-            k_dn_resid<<<nblk, kDnBlock, 0, q>>>(a);
+            launch_pdl(k_dn_resid, dim3(nblk), dim3(kDnBlock), 0, q, a);
         }
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->dn_pin, &a.sc->done, sizeof(int), cudaMemcpyDeviceToHost, q);
