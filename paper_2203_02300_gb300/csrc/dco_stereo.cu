@@ -55,14 +55,32 @@ __device__ __forceinline__ uint32_t spread10(uint32_t c)
 {
     return (c & 0xffu) | ((c & 0xff00u) << 2) | ((c & 0xff0000u) << 4);
 }
-// back to bytes r | g<<8 | b<<16
+// back to bytes r | g<<8 | b<<16 (bits 30, 31 ignored)
 __device__ __forceinline__ uint32_t unspread10(uint32_t e)
 {
     return (e & 0xffu) | ((e >> 2) & 0xff00u) | ((e >> 4) & 0xff0000u);
 }
 
+// The two bits above the fields of a packed colour: every arm step's colour
+// difference to its predecessor must be below tau1 (Sect. 4.1), a property
+// of the pixel edge alone, so k_pack stores it once per pixel: bit 30 for
+// the edge to the left neighbour, bit 31 for the edge to the one above.
+constexpr uint32_t kEdgeL = 1u << 30, kEdgeU = 1u << 31, kColour = 0x3fffffffu;
+
+// all channels within tau of p, given Kp = K - E(p) and pK = E(p) + K
+__device__ __forceinline__ bool within(uint32_t ec, uint32_t Kp, uint32_t pK)
+{
+    return ((ec + Kp) & (pK - ec) & kM9) == kM9;
+}
+
+__device__ __forceinline__ uint32_t rgb_at(const uint8_t *rgb, size_t i)
+{
+    const uint8_t *p = rgb + 3 * i;
+    return uint32_t(__ldg(p)) | (uint32_t(__ldg(p + 1)) << 8) | (uint32_t(__ldg(p + 2)) << 16);
+}
+
 // k_pack stores every colour spread (the arm walks read each candidate many
-// times; the record keeps the bytes)
+// times; the record keeps the bytes) with its two edge bits
 __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   // pixels 4q .. 4q+3
 {
     const int i0 = 4 * q;
@@ -85,13 +103,50 @@ __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   /
             c[k] = uint32_t(__ldg(p)) | (uint32_t(__ldg(p + 1)) << 8) | (uint32_t(__ldg(p + 2)) << 16);
         }
     }
+    // edge bits: the left neighbour (pixel i - 1 in the same row) and the
+    // one above (pixel i - W)
+    uint32_t e[4], u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) e[k] = spread10(c[k]);
+    const int W = a.W;
+    const int up0 = i0 - W;
+    if (up0 >= 0 && i0 + 4 <= a.npx && ((reinterpret_cast<uintptr_t>(rgb + 3 * (size_t)up0) & 3u) == 0)) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * (size_t)up0);
+        const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+        u[0] = w0 & 0x00ffffffu;
+        u[1] = __funnelshift_r(w0, w1, 24) & 0x00ffffffu;
+        u[2] = __funnelshift_r(w1, w2, 16) & 0x00ffffffu;
+        u[3] = w2 >> 8;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) u[k] = up0 + k >= 0 ? rgb_at(rgb, (size_t)min(up0 + k, a.npx - 1)) : 0u;
+    }
+    // pixel i0 - 1: the top three bytes of the word before this group (the
+    // group starts 4-byte aligned on the aligned path)
+    uint32_t prev = 0u;
+    if (i0 > 0)
+        prev = spread10(((reinterpret_cast<uintptr_t>(rgb) & 3u) == 0)
+                            ? __ldg(reinterpret_cast<const uint32_t *>(rgb + 3 * (size_t)i0) - 1) >> 8
+                            : rgb_at(rgb, (size_t)(i0 - 1)));
+    int x = i0 % W;
+    uint32_t out[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t Kp = a.k1 - e[k], pK = e[k] + a.k1;
+        uint32_t v = e[k];
+        if (x > 0 && within(prev, Kp, pK)) v |= kEdgeL;
+        if (up0 + k >= 0 && within(spread10(u[k]), Kp, pK)) v |= kEdgeU;
+        out[k] = v;
+        prev = e[k];
+        x = x + 1 == W ? 0 : x + 1;
+    }
     if (i0 + 4 <= a.npx) {
-        *reinterpret_cast<uint4 *>(rgbx + i0) = make_uint4(spread10(c[0]), spread10(c[1]), spread10(c[2]), spread10(c[3]));
+        *reinterpret_cast<uint4 *>(rgbx + i0) = make_uint4(out[0], out[1], out[2], out[3]);
         *reinterpret_cast<uint32_t *>(grey + i0) =
             grey_of(c[0]) | (grey_of(c[1]) << 8) | (grey_of(c[2]) << 16) | (grey_of(c[3]) << 24);
     } else {
         for (int k = 0; i0 + k < a.npx; k++) {
-            rgbx[i0 + k] = spread10(c[k]);
+            rgbx[i0 + k] = out[k];
             grey[i0 + k] = (uint8_t)grey_of(c[k]);
         }
     }
@@ -106,12 +161,6 @@ __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   /
 constexpr int kTX = 32, kTY = 8;
 constexpr int kMaxCW = 15, kMaxCH = 15;
 constexpr int kGW = 48;   // grey tile row pitch (>= kTX + kMaxCW - 1, multiple of 4)
-
-// all channels within tau of p, given Kp = K - E(p) and pK = E(p) + K
-__device__ __forceinline__ bool within(uint32_t ec, uint32_t Kp, uint32_t pK)
-{
-    return ((ec + Kp) & (pK - ec) & kM9) == kM9;
-}
 
 // 4 flags f_i = [byte_i(w) < byte_i(c4)] -> bits f0 | f1<<1 | f2<<2 | f3<<3.
 // Per byte: (w|0x80) - (c&0x7f) never borrows into the next byte, and its top
@@ -186,20 +235,22 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
 
     // arms: largest k <= L1 whose steps all pass the double threshold
     const size_t i = (size_t)y * W + x;
-    const uint32_t p = __ldg(rgbx + i);   // colours are stored spread (k_pack)
+    const uint32_t praw = __ldg(rgbx + i);   // colours are stored spread (k_pack), with edge bits
+    const uint32_t p = praw & kColour;
     const int L1 = a.L1, L2 = a.L2;
     // K = t - 1 + 512 in each 10-bit field, t = min(tau, 256): the field of
     // E(c) + K - E(q) has bit 9 set exactly when c - q > -t, and with t = 256
     // every pair passes (a threshold of 256 or more never stops an arm).
     // Up to L2 a step is tested against p with tau1; beyond L2 against p
-    // with min(tau1, tau2) (both must hold); always against its predecessor
-    // with tau1.  One test covers both comparisons, the predecessor's
-    // constants carried from the previous step.
+    // with min(tau1, tau2) (both must hold).  The test against the step's
+    // predecessor (tau1) is the edge bit k_pack stored: the candidate's own
+    // for walks right and down (its edge towards p), the predecessor's for
+    // walks left and up.
     auto kfield = [](int tau) { return 0x00100401u * (uint32_t)(min(tau, 256) + 511); };
     const uint32_t k1 = kfield(a.tau1), k2 = kfield(min(a.tau1, a.tau2));
     const uint32_t K1p = k1 - p, pK1 = p + k1, K2p = k2 - p, pK2 = p + k2;
-    auto pass = [](uint32_t c, uint32_t Kp, uint32_t pK, uint32_t kq, uint32_t qk) {
-        return ((c + Kp) & (pK - c) & (c + kq) & (qk - c) & kM9) == kM9;
+    auto pass = [](uint32_t c, uint32_t Kp, uint32_t pK, uint32_t ew, uint32_t bit) {
+        return ((((c + Kp) & (pK - c)) & kM9 | (ew & bit)) == (kM9 | bit));
     };
     // the first kArmBatch candidates of all four directions are loaded at
     // once (in-image addresses only), so a typical pixel pays one load latency
@@ -219,17 +270,19 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     }
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        uint32_t kq = k1 - p, qk = p + k1;   // predecessor constants (p itself before step 1)
+        const uint32_t bit = e < 2 ? kEdgeL : kEdgeU;
+        const bool own = e & 1;   // right, down: the candidate's own edge bit
+        uint32_t prev = praw;     // left, up: the predecessor's (p itself before step 1)
         int n = 0;
         bool open = true;
 #pragma unroll
         for (int u = 0; u < kArmBatch; u++) {
             const int j = u + 1;
             const bool far = j > L2;
-            if (open && j <= lim[e] && pass(cand[e][u], far ? K2p : K1p, far ? pK2 : pK1, kq, qk)) {
+            const uint32_t c = cand[e][u];
+            if (open && j <= lim[e] && pass(c, far ? K2p : K1p, far ? pK2 : pK1, own ? c : prev, bit)) {
                 n = j;
-                kq = k1 - cand[e][u];
-                qk = cand[e][u] + k1;
+                prev = c;
             } else {
                 open = false;
             }
@@ -238,20 +291,33 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
         if (open) {
             const uint32_t *q = rgbx + i + (ptrdiff_t)n * step[e];
             int j = n + 1;
-            for (const int l = min(lim[e], L2); j <= l; j++) {
-                q += step[e];
-                const uint32_t c = __ldg(q);
-                if (!pass(c, K1p, pK1, kq, qk)) { open = false; break; }
-                kq = k1 - c;
-                qk = c + k1;
-            }
-            if (open) {
-                for (; j <= lim[e]; j++) {
+            if (own) {
+                for (const int l = min(lim[e], L2); j <= l; j++) {
                     q += step[e];
                     const uint32_t c = __ldg(q);
-                    if (!pass(c, K2p, pK2, kq, qk)) break;
-                    kq = k1 - c;
-                    qk = c + k1;
+                    if (!pass(c, K1p, pK1, c, bit)) { open = false; break; }
+                }
+                if (open) {
+                    for (; j <= lim[e]; j++) {
+                        q += step[e];
+                        const uint32_t c = __ldg(q);
+                        if (!pass(c, K2p, pK2, c, bit)) break;
+                    }
+                }
+            } else {
+                for (const int l = min(lim[e], L2); j <= l; j++) {
+                    q += step[e];
+                    const uint32_t c = __ldg(q);
+                    if (!pass(c, K1p, pK1, prev, bit)) { open = false; break; }
+                    prev = c;
+                }
+                if (open) {
+                    for (; j <= lim[e]; j++) {
+                        q += step[e];
+                        const uint32_t c = __ldg(q);
+                        if (!pass(c, K2p, pK2, prev, bit)) break;
+                        prev = c;
+                    }
                 }
             }
             n = j - 1;
@@ -1687,6 +1753,8 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
             a.a.grey[v] = jptr<uint8_t>(h, j, j.L.grey[v]);
         }
         a.a.npx = npx;
+        a.a.W = j.W;
+        a.a.k1 = 0x00100401u * (uint32_t)(std::min(p.tau1, 256) + 511);   // tau1 in every 10-bit field
         a.gx = (npx + 1023) / 1024;   // 256 threads x 4 pixels
         a.gy = nimg;
         a.gz = 1;

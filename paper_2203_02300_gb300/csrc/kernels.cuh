@@ -49,7 +49,8 @@ struct PackArgs {
     const uint8_t *rgb[2];
     uint32_t *rgbx[2];
     uint8_t *grey[2];
-    int npx;
+    int npx, W;
+    uint32_t k1;           // colour threshold tau1 in every 10-bit field (see kM9)
 };
 
 struct PrepArgs {
