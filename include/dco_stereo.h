@@ -224,8 +224,8 @@ dco_status dco_stereo_cost_volume(dco_stereo *h, const uint8_t *left, const uint
  *   d'(p) = argmax_d hist(d, N_p)
  * over the valid pixels of the support region N_p of Eq. 2 (the arms of
  * `rgb`, the reference image, under p's arm parameters); the smallest d on
- * equal counts.  Pixels of disp_in outside [0, D-1] (-1 = invalid) cast no
- * vote and are written as -1.  Each round reads the whole previous map.
+ * equal counts.  Pixels of disp_in outside [p->d_min, p->d_min + D - 1]
+ * (-1 = invalid) cast no vote and are written as -1.  Each round reads the whole previous map.
  * rgb: device W*H*3 bytes; disp_in, disp_out: device W*H int16 (may be the
  * same buffer).  0 rounds copies the map.  Same errors as dco_stereo_match.
  */

@@ -5,7 +5,8 @@
 // outlier removal by left-right consistency, Sect. 4.3).
 //
 // Pipeline per pair (one stream, no host round trip):
-//   k_pack   RGB -> packed colour words and the grey level, both images
+//   k_pack   RGB -> packed colour words (with the two edge bits of the arm
+//            rule's predecessor test) and the grey level, both images
 //   k_prep   census (shared-memory grey tile) + the four arms (walks over the
 //            packed colours) -> 16-byte records + arm words
 //   per pass of dc disparities:
@@ -16,6 +17,8 @@
 //             over the up/down arms (Eq. 2) and the running minimum over
 //             the disparities (Eq. 3), merged with the previous passes
 //   k_lr     left-right consistency -> disparity map
+// Every kernel is launched with programmatic stream serialization and waits
+// for its predecessors before its first global access.
 // Lanes of a warp hold consecutive disparities of one pixel (pairs of them
 // in k_hagg's cost phase): the reference record is a broadcast load, the
 // candidates are consecutive records, prefix rows hit distinct banks, and
