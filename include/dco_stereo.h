@@ -440,9 +440,12 @@ dco_status dco_stereo_noalloc_status(dco_stream stream);
  *   DCO_EBUDGET if a lane's share cannot hold one frame of the largest
  *   stream.
  * dco_server_submit: left, right (W*H*3 bytes) and disp_out (W*H int16) are
- *   host buffers of the stream's shape (pinned memory makes the copies
- *   asynchronous) that must stay valid until dco_server_wait returns for
- *   the ticket; returns at once with the request's ticket.
+ *   host buffers of the stream's shape that must stay valid until
+ *   dco_server_wait returns for the ticket; returns at once with the
+ *   request's ticket.  When all three are device-accessible (pinned,
+ *   registered or managed memory) and p->vote_iters is 0, the kernels read
+ *   and write them in place; otherwise they are copied through the
+ *   stream's device slots.
  * dco_server_wait: blocks until the request is done (timeout_ms < 0: no
  *   limit; DCO_ETIMEOUT when the limit passes first, the request still
  *   pending), fills *times (may be NULL) and returns the request's status

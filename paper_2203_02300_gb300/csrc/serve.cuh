@@ -29,6 +29,7 @@ struct SrvReq {
     int stream = 0, slot = -1;
     const uint8_t *left = nullptr, *right = nullptr;
     int16_t *out = nullptr;
+    bool direct = false;   // all three buffers device-accessible: no staging copies
     unsigned long long ticket = 0;
     double arrival = 0, launch = 0, done = 0;
     float device_ms = 0;
@@ -167,6 +168,10 @@ dco_status srv_launch(dco_server *s, SrvLane &ln, const std::vector<SrvReq *> &b
         const SrvReq *r = batch[k];
         const dco_stream_desc &d = s->streams[r->stream];
         const SrvSlot &sl = s->slots[r->stream][r->slot];
+        if (r->direct) {   // the device reads the images and writes the map in place
+            descs[k] = dco_pair_desc{r->left, r->right, d.W, d.H, d.D, r->out, d.d_chunk, d.h_chunk, d.v_chunk};
+            continue;
+        }
         const size_t img = (size_t)d.W * d.H * 3;
         if (cudaMemcpyAsync(sl.left, r->left, img, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
             cudaMemcpyAsync(sl.right, r->right, img, cudaMemcpyHostToDevice, cs) != cudaSuccess)
@@ -176,6 +181,7 @@ dco_status srv_launch(dco_server *s, SrvLane &ln, const std::vector<SrvReq *> &b
     dco_status st = dco_stereo_match_batch(ln.h, descs.data(), (int)descs.size(), &s->params, cs);
     if (st != DCO_OK) return st;
     for (const SrvReq *r : batch) {
+        if (r->direct) continue;
         const dco_stream_desc &d = s->streams[r->stream];
         const SrvSlot &sl = s->slots[r->stream][r->slot];
         if (cudaMemcpyAsync(r->out, sl.out, (size_t)d.W * d.H * 2, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -400,6 +406,11 @@ dco_status dco_server_submit(dco_server *s, int stream, const uint8_t *left, con
     r->left = left;
     r->right = right;
     r->out = disp_out;
+    // pinned, registered or managed host buffers are read and written by the
+    // kernels in place (over NVLink-C2C on Grace systems), as in
+    // dco_stereo_match_host; other buffers go through the stream's device slots
+    r->direct = s->params.vote_iters == 0 && device_accessible(left) && device_accessible(right) &&
+                device_accessible(disp_out);
     r->arrival = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);
