@@ -171,3 +171,29 @@ def test_native_runtime_with_latency_critical_streams_equals_alone(env):
     for (i, k), got in outs.items():
         assert np.array_equal(got, alone[(i, k % 4)]), (i, k)
     assert stats["frames"] == 16 * len(SHAPES)
+
+
+def test_native_runtime_pageable_and_pinned_buffers(env):
+    # pinned buffers are read and written in place by the kernels, pageable
+    # ones go through the stream's device slots; both give the map matched
+    # alone, also mixed within one stream
+    torch, binding, st = env
+    from paper_2203_02300_gb300 import scenes
+    W, H, D = SHAPES[1]
+    sc = [scenes.StreamScene(1, W, H, D).frame(t) for t in range(4)]
+    alone = [st.match(torch.from_numpy(s.left).cuda(), torch.from_numpy(s.right).cuda(), D).cpu().numpy() for s in sc]
+    jobs = []
+    with binding.NativeServer([(W, H, D)], lanes=2, slots_per_stream=2) as srv:
+        for k, s in enumerate(sc * 3):
+            pinned = k % 2 == 0
+            if pinned:
+                l = torch.from_numpy(s.left).pin_memory().numpy()
+                r = torch.from_numpy(s.right).pin_memory().numpy()
+                o = torch.full((H, W), -9, dtype=torch.int16).pin_memory().numpy()
+            else:
+                l, r, o = s.left.copy(), s.right.copy(), np.full((H, W), -9, np.int16)
+            jobs.append((k % 4, o, srv.submit(0, l, r, o)))
+        for k, o, t in jobs:
+            srv.wait(t, timeout_ms=60000)
+    for k, o, t in jobs:
+        assert np.array_equal(o, alone[k]), k
