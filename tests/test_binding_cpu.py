@@ -56,3 +56,40 @@ def test_tile_candidates_follow_the_block_limits():
             assert len(set(counts)) == len(counts)
             assert len(set(hs)) == len(hs)
     assert Tile.of(None) == Tile() and Tile.of(64) == Tile(64, 0, 0) and Tile.of((32, 96, 120)) == Tile(32, 96, 120)
+
+
+def test_tuner_coordinate_search_and_cache(tmp_path, monkeypatch):
+    # the tuner's host logic with a fake timer: the pass width first, then the
+    # first pass's blocks, then the second's; a change only when more than 1 %
+    # faster; the winner cached per shape and read back
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_02300_gb300 import tune
+    from paper_2203_02300_gb300.binding import Tile
+    monkeypatch.setenv("DCO_TUNE_CACHE", str(tmp_path / "tiles.json"))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a, **k: "fake GPU")
+    W, H, D = 640, 480, 128
+    cost = {}
+
+    def ms(t):
+        base = {32: 1.0, 64: 0.8, 96: 0.795, 128: 0.7}[t.d_chunk]   # 96: within 1 % of 64 (kept 64); 128 wins
+        h = {0: 0.0, 320: -0.05, 224: -0.004, 160: 0.02, 128: 0.03, 96: 0.04}[t.h_chunk]
+        v = {0: 0.0, 240: 0.01, 160: -0.03, 120: -0.0301, 96: 0.0, 80: 0.05}[t.v_chunk]
+        return base + h + v
+
+    class FakeStereo:
+        def match(self, left, right, D, p, out):
+            cost["last"] = Tile(p.d_chunk, p.h_chunk, p.v_chunk)
+
+    def fake_time(fn, reps):
+        fn()
+        return ms(cost["last"])
+    monkeypatch.setattr(tune, "_time_call", fake_time)
+    left = torch.zeros((H, W, 3), dtype=torch.uint8)
+    won = tune.tune_tiles(FakeStereo(), left, left, D)
+    # 128 beats 64 by far; h 320 beats 0 by 5 %; v 160 beats 0 by 3 % and
+    # 120 is not 1 % better than 160
+    assert won == Tile(128, 320, 160)
+    assert tune.lookup(W, H, D, "fake GPU") == won
+    monkeypatch.setattr(tune, "_time_call", lambda fn, reps: (_ for _ in ()).throw(AssertionError("timed again")))
+    assert tune.tune_tiles(FakeStereo(), left, left, D) == won   # from the cache
