@@ -176,6 +176,33 @@ def test_ragged_sizes(env, W, H, D):
     full_check(env, left, right, D)
 
 
+def test_maximum_width(env):
+    # the widest rows (16384 columns: 32 first-pass blocks of 512 per row) at
+    # the largest range D = 256
+    s = scenes.plane_scene(16384, 12, 256, 40, seed=scenes.seed_for(1, 500), drange=(2, 250), noise_sigma=2.0)
+    full_check(env, s.left, s.right, 256, label="16384x12 D=256")
+
+
+def test_maximum_height(env):
+    # the tallest columns (16384 rows: 38 second-pass blocks per column),
+    # sampled row bands against the oracle (census and arms of the whole image)
+    torch, binding, st = env
+    s = scenes.plane_scene(48, 16384, 24, 30, seed=scenes.seed_for(1, 501), drange=(2, 22), noise_sigma=2.0)
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, 24)
+    tl, tr, tf = (parity.Tally(f"48x16384 D=24 {v}") for v in ("left disparity", "right disparity", "final map"))
+    for rows in ((0, 48), (8170, 8218), (16336, 16384)):
+        ref = O.match(s.left, s.right, 24, rows=rows, quantized=True)
+        sl = slice(*rows)
+        what = f"48x16384 rows {rows[0]}-{rows[1]}"
+        parity.check_disparity(dl[sl], ref.disp_l, ref.best_l, ref.second_l, what + " left", ref.qdisp_l, tally=tl)
+        parity.check_disparity(dr[sl], ref.disp_r, ref.best_r, ref.second_r, what + " right", ref.qdisp_r, tally=tr)
+        parity.check_cost(cl[sl], ref.best_l, dl[sl], ref.disp_l)
+        parity.check_cost(cr[sl], ref.best_r, dr[sl], ref.disp_r)
+        parity.check_final(out[sl], ref, what + " final map", tally=tf)
+    for t in (tl, tr, tf):
+        t.close()
+
+
 @pytest.mark.parametrize("chunk", [1, 5, 16, 32, 33, 64])
 def test_passes_are_bit_identical(env, chunk):
     torch, binding, st = env
@@ -480,8 +507,12 @@ def test_argument_errors(env):
     assert lib.dco_stereo_match(h, None, L.data_ptr(), 8, 8, 4, None, out.data_ptr(), s0) == binding.DCO_EINVAL
     assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 4, None, None, s0) == binding.DCO_EINVAL
     assert lib.dco_stereo_match(None, L.data_ptr(), L.data_ptr(), 8, 8, 4, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 0, 1, None, out.data_ptr(), s0) == binding.DCO_EINVAL
+    assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 16385, 1, 1, None, out.data_ptr(),
+                                s0) == binding.DCO_EINVAL
     for bad in (dict(census_w=8), dict(census_w=13, census_h=7), dict(arm_l1=41), dict(arm_l1=0),
-                dict(lambda_ad=0.0), dict(eps=-1.0), dict(d_chunk=-1)):
+                dict(lambda_ad=0.0), dict(eps=-1.0), dict(d_chunk=-1), dict(d_min=-1), dict(d_min=5),
+                dict(h_chunk=8), dict(v_chunk=-2)):
         p = binding.Params.default(**bad)
         import ctypes
         assert lib.dco_stereo_match(h, L.data_ptr(), L.data_ptr(), 8, 8, 4, ctypes.byref(p), out.data_ptr(),
