@@ -14,8 +14,12 @@
  * Conventions shared by every entry point
  *   - Images are interleaved RGB uint8, row-major, pitch 3*W bytes, no
  *     padding (pixel (x, y) channel c at byte 3*(y*W + x) + c).
- *   - Disparities are int16, row-major W*H, d in [0, D-1]; -1 = invalid
- *     (rejected by the consistency check).
+ *   - Disparities are int16, row-major W*H, d in [d_min, d_min + D - 1]
+ *     (p->d_min, 0 by default); -1 = invalid (rejected by the consistency
+ *     check).
+ *   - Kernels are launched with programmatic stream serialization (each
+ *     waits for the preceding work of its stream before touching memory),
+ *     so a launch overlaps the end of the previous one on the stream.
  *   - "device" pointers must be CUDA device memory (or managed memory) of
  *     the device the handle was created on; "host" pointers are ordinary
  *     (preferably pinned) host memory.  The caller owns every buffer it
