@@ -706,13 +706,21 @@ def batch_config5(torch, binding, flush, dev, reps: int = 3, budget: int = 1_500
     pairs = [(torch.from_numpy(s.left).to(dev), torch.from_numpy(s.right).to(dev), s.D,
               torch.empty((s.H, s.W), dtype=torch.int16, device=dev)) for s in sc]
     units = sum(s.W * s.H * s.D for s in sc)
+    from paper_2203_02300_gb300 import tune
     with binding.Stereo(dev.index or 0, budget_bytes=budget) as h:
         t = _timed(torch, dev, flush, lambda: h.match_batch(pairs), reps)
         h.stream_status()
         alloc, groups = h.workspace_allocated(), h.batch_groups()
+        # the blocks of the two 1-D passes from the autotuner (passes of 32
+        # disparities, as the budget admits them)
+        tile = tune.tune_shape(h, 1920, 1080, 256, device=dev.index or 0, max_slice_bytes=8 * 1920 * 1080 * 32)
+        tuned = [p + (tile,) for p in pairs]
+        t_tuned = _timed(torch, dev, flush, lambda: h.match_batch(tuned), reps)
+        h.stream_status()
     return {"pairs": 8, "size": "1920x1080 D=256", "evals": units, "budget_bytes": budget,
             "one_volume_bytes": 1920 * 1080 * 256 * 4, "workspace_allocated_bytes": alloc,
-            "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3)}
+            "admission_groups": groups, "ms": t, "evals_per_s": units / (t * 1e-3),
+            "tuned_tile_d_h_v": list(tile), "tuned_ms": t_tuned, "tuned_evals_per_s": units / (t_tuned * 1e-3)}
 
 
 def serve_config4_native(torch, binding, st, device: int, time_scale: float = 1.0, frames=None, tiles=None,
