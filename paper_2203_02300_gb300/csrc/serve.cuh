@@ -104,9 +104,6 @@ cudaEvent_t srv_event(dco_server *s)
     return e;
 }
 
-// Admit pending requests in arrival order while the batch has room, the
-// request's stream has a free slot and the lane's share of the budget holds
-// its workspace; the ones left behind keep their order.  Caller holds mu.
 // a pending frame of stream `st` can be admitted now (a free slot)
 bool srv_slot_free(const dco_server *s, int st)
 {
@@ -117,7 +114,9 @@ bool srv_slot_free(const dco_server *s, int st)
 
 // The next batch: frames of latency-critical streams first (a batch holds
 // frames of one class only), in arrival order within the class, while the
-// frame's stream has a free slot and the batch fits the lane's budget.
+// batch has room, the frame's stream has a free slot and the lane's share
+// of the budget holds its workspace; the frames left behind keep their
+// order.  Caller holds mu.
 std::vector<SrvReq *> srv_form_batch(dco_server *s, bool &hi)
 {
     std::vector<SrvReq *> batch;
