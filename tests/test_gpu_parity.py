@@ -485,6 +485,19 @@ def test_match_host_equals_device_path(env):
     assert np.array_equal(want, st.match_host(Lp, Rp, s.D, pv, out=op))
 
 
+@pytest.mark.parametrize("config", [1, 2])
+def test_mirror_swap_symmetry_on_the_gpu(env, config):
+    # swapping the views and mirroring both rows exchanges the two reference
+    # views: the kernels' integer region sums run the other way along the
+    # rows and give the same fixed-point values, so the maps mirror exactly
+    torch, binding, st = env
+    s = scenes.config_scene(config)
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
+    mout, mdl, mdr, mcl, mcr = run_views(env, s.right[:, ::-1], s.left[:, ::-1], s.D)
+    assert np.array_equal(mdl, dr[:, ::-1]) and np.array_equal(mdr, dl[:, ::-1])
+    assert np.array_equal(mcl, cr[:, ::-1]) and np.array_equal(mcr, cl[:, ::-1])
+
+
 def test_repeat_runs_bit_identical(env):
     s = scenes.config_scene(2)
     a = run_views(env, s.left, s.right, s.D)
