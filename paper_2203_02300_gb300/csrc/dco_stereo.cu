@@ -155,6 +155,81 @@ __device__ __forceinline__ void pack_body(const PackArgs &a, int q, int img)   /
     }
 }
 
+// The same for images in host memory (read over NVLink-C2C, where every
+// extra read costs): one thread per block of 4 columns x kRows rows, so the
+// row above is read once per block instead of once per row.
+template <int kRows>
+__device__ __forceinline__ void pack_rows_body(const PackArgs &a, int t, int img)
+{
+    const int W = a.W, H = a.npx / W;
+    const int ngx = (W + 3) >> 2, nby = (H + kRows - 1) / kRows;
+    const int band = t / ngx, qx = t - band * ngx;
+    if (band >= nby) return;
+    const int x0 = 4 * qx, y0 = kRows * band, nx = min(4, W - x0);
+    const uint8_t *rgb = img ? a.rgb[1] : a.rgb[0];
+    uint32_t *rgbx = img ? a.rgbx[1] : a.rgbx[0];
+    uint8_t *grey = img ? a.grey[1] : a.grey[0];
+    // rows start 4-byte aligned in the input and 16-byte aligned in the
+    // outputs when W is a multiple of 4
+    const bool vec = nx == 4 && (W & 3) == 0 && (reinterpret_cast<uintptr_t>(rgb) & 3u) == 0;
+    // the four colours of row y at x0 .. x0 + 3 (repeating the last one past
+    // the row's end) and the left neighbour (x0 - 1)
+    auto load_row = [&](int y, uint32_t (&c)[4], uint32_t &left) {
+        const size_t i = (size_t)y * W + x0;
+        if (vec) {
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(rgb + 3 * i);
+            const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+            c[0] = w0 & 0x00ffffffu;
+            c[1] = __funnelshift_r(w0, w1, 24) & 0x00ffffffu;
+            c[2] = __funnelshift_r(w1, w2, 16) & 0x00ffffffu;
+            c[3] = w2 >> 8;
+            left = x0 > 0 ? __ldg(w - 1) >> 8 : 0u;   // the top three bytes of the word before
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) c[k] = rgb_at(rgb, i + min(k, nx - 1));
+            left = x0 > 0 ? rgb_at(rgb, i - 1) : 0u;
+        }
+    };
+    uint32_t up[4] = {0u, 0u, 0u, 0u};   // spread colours of the row above
+    if (y0 > 0) {
+        uint32_t c[4], l;
+        load_row(y0 - 1, c, l);
+#pragma unroll
+        for (int k = 0; k < 4; k++) up[k] = spread10(c[k]);
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+        const int y = y0 + r;
+        if (y >= H) break;
+        uint32_t c[4], l, e[4], out[4];
+        load_row(y, c, l);
+#pragma unroll
+        for (int k = 0; k < 4; k++) e[k] = spread10(c[k]);
+        uint32_t prev = spread10(l);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t Kp = a.k1 - e[k], pK = e[k] + a.k1;
+            uint32_t v = e[k];
+            if (x0 + k > 0 && within(prev, Kp, pK)) v |= kEdgeL;
+            if (y > 0 && within(up[k], Kp, pK)) v |= kEdgeU;
+            out[k] = v;
+            prev = e[k];
+            up[k] = e[k];
+        }
+        const size_t i = (size_t)y * W + x0;
+        if (vec) {
+            *reinterpret_cast<uint4 *>(rgbx + i) = make_uint4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<uint32_t *>(grey + i) =
+                grey_of(c[0]) | (grey_of(c[1]) << 8) | (grey_of(c[2]) << 16) | (grey_of(c[3]) << 24);
+        } else {
+            for (int k = 0; k < nx; k++) {
+                rgbx[i + k] = out[k];
+                grey[i + k] = (uint8_t)grey_of(c[k]);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ k_prep
 // One thread per pixel of a 32 x 8 tile.  Census (Sect. 4.2.1) from the grey
 // tile with its window halo in shared memory (clamp-to-edge on load); the
@@ -1152,13 +1227,16 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ Batch<Sm
     smooth_body<kMax>(b.p[i], bx * 256 + threadIdx.x, by);
 }
 
-template <int N>
+// kRows 0: the flat mapping (images in device memory); else blocks of
+// kRows rows per thread (images in host memory)
+template <int N, int kRows = 0>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Batch<PackArgs, N> b)
 {
     pdl_enter();
     int bx, by, bz;
     const int i = batch_pair(b, blockIdx.x, bx, by, bz);
-    pack_body(b.p[i], bx * 256 + threadIdx.x, by);
+    if (kRows == 0) pack_body(b.p[i], bx * 256 + threadIdx.x, by);
+    else pack_rows_body<kRows ? kRows : 1>(b.p[i], bx * 256 + threadIdx.x, by);
 }
 
 template <int CW, int CH, int N>
@@ -1742,10 +1820,23 @@ template <class T>
 T *jptr(dco_stereo *h, const Job &j, size_t off) { return ws_ptr<T>(h, j.base + off); }
 
 // grey/colour packing and census + arms for nimg images of every job
+// images the kernels read from host memory (pinned or registered; over
+// NVLink-C2C on Grace systems)
+constexpr int kPackHostRows = 4;   // rows per k_pack thread for those
+bool in_host_memory(const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
 dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, const std::vector<Job> &jobs,
                        int nimg, cudaStream_t s)
 {
-    std::vector<Item<PackArgs>> pk;
+    std::vector<Item<PackArgs>> pk, pk_host;
     std::vector<Item<PrepArgs>> pr;
     for (const Job &j : jobs) {
         const int npx = j.W * j.H;
@@ -1758,10 +1849,15 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
         a.a.npx = npx;
         a.a.W = j.W;
         a.a.k1 = 0x00100401u * (uint32_t)(std::min(p.tau1, 256) + 511);   // tau1 in every 10-bit field
-        a.gx = (npx + 1023) / 1024;   // 256 threads x 4 pixels
         a.gy = nimg;
         a.gz = 1;
-        pk.push_back(a);
+        if (in_host_memory(j.left) || in_host_memory(j.right)) {
+            a.gx = (((j.W + 3) / 4) * ((j.H + kPackHostRows - 1) / kPackHostRows) + 255) / 256;
+            pk_host.push_back(a);
+        } else {
+            a.gx = (npx + 1023) / 1024;   // 256 threads x 4 pixels
+            pk.push_back(a);
+        }
         Item<PrepArgs> b{};
         for (int v = 0; v < 2; v++) {
             b.a.rgbx[v] = jptr<uint32_t>(h, j, j.L.rgbx[v]);
@@ -1780,6 +1876,8 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
         pr.push_back(b);
     }
     dco_status st = launch_items(h, s, "k_pack", k_pack<1>, k_pack<kBatchMax>, pk, 256, 0);
+    if (st != DCO_OK) return st;
+    st = launch_items(h, s, "k_pack", k_pack<1, kPackHostRows>, k_pack<kBatchMax, kPackHostRows>, pk_host, 256, 0);
     if (st != DCO_OK) return st;
     if (p.census_w == 9 && p.census_h == 7)
         st = launch_items(h, s, "k_prep", k_prep<9, 7, 1>, k_prep<9, 7, kBatchMax>, pr, kTX * kTY, 0);
