@@ -189,8 +189,14 @@ def _ptr(t) -> int:
 
 
 def _stream(stream) -> Optional[int]:
+    """The cudaStream_t of `stream` (None: torch's current stream on the
+    current device)."""
     if stream is None:
         import torch
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        dev = getattr(torch._C, "_cuda_getDevice", None)
+        if raw is not None and dev is not None:   # the same stream, without a Stream object (0.2 against 3 us)
+            return raw(dev())
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, int):
         return stream
@@ -205,10 +211,13 @@ def _contiguous(t) -> bool:
     return t.flags.c_contiguous if _is_np(t) else t.is_contiguous()
 
 
+_NP_DTYPES = {n: np.dtype(n) for n in ("uint8", "int16", "float32", "int64")}
+
+
 def _dtype_ok(t, name: str) -> bool:
     """t's element type is `name` ("uint8", "int16", "float32", "int64")."""
     if _is_np(t):
-        return t.dtype == np.dtype(name)
+        return t.dtype == _NP_DTYPES[name]
     import torch
     return t.dtype == getattr(torch, name)
 

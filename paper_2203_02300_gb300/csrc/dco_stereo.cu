@@ -1784,6 +1784,7 @@ struct Job {
     uchar4 *arms0 = nullptr;   // stage entry point: arms of image 0 go here
     int dchunk = 0;                  // this pair's pass width (0: the call's parameters)
     int hchunk = 0, vchunk = 0;      // this pair's tile shapes (0: the call's parameters)
+    int host_in = -1;                // images in host memory: 1, in device memory: 0, -1: ask the driver
     const int16_t *vsrc = nullptr;   // Eq. 4 round: map voted on (null: no vote)
     int16_t *vdst = nullptr;         //   and the map written
     Layout L{};
@@ -1851,7 +1852,7 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
         a.a.k1 = 0x00100401u * (uint32_t)(std::min(p.tau1, 256) + 511);   // tau1 in every 10-bit field
         a.gy = nimg;
         a.gz = 1;
-        if (in_host_memory(j.left) || in_host_memory(j.right)) {
+        if (j.host_in > 0 || (j.host_in < 0 && (in_host_memory(j.left) || in_host_memory(j.right)))) {
             a.gx = (((j.W + 3) / 4) * ((j.H + kPackHostRows - 1) / kPackHostRows) + 255) / 256;
             pk_host.push_back(a);
         } else {
@@ -2218,11 +2219,12 @@ dco_status check_common(dco_stereo *h, const dco_params *pin, dco_params &p)
 
 dco_status run_match(dco_stereo *h, const uint8_t *left, const uint8_t *right, int W, int H, int D,
                      const dco_params &p, int16_t *disp_out, int16_t *disp_l, int16_t *disp_r,
-                     float *cost_l, float *cost_r, float *vol, int vol_view, cudaStream_t s)
+                     float *cost_l, float *cost_r, float *vol, int vol_view, cudaStream_t s, int host_in = -1)
 {
     std::vector<Job> jobs(1);
     Job &j = jobs[0];
     j.left = left; j.right = right; j.W = W; j.H = H; j.D = D;
+    j.host_in = host_in;
     j.out = disp_out; j.disp_l = disp_l; j.disp_r = disp_r;
     j.cost_l = cost_l; j.cost_r = cost_r; j.vol = vol; j.vol_view = vol_view;
     return run_jobs(h, p, jobs, s);
@@ -2385,7 +2387,7 @@ dco_status dco_stereo_match_host(dco_stereo *h, const uint8_t *left_host, const 
     if (device_accessible(left_host) && device_accessible(right_host) && device_accessible(disp_host) &&
         p.vote_iters == 0) {
         st = run_match(h, left_host, right_host, W, H, D, p, disp_host, nullptr, nullptr, nullptr, nullptr, nullptr,
-                       0, s);
+                       0, s, 1);
         if (st != DCO_OK) return st;
         DCO_CUDA(h, cudaStreamSynchronize(s));
         return DCO_OK;
