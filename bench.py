@@ -80,15 +80,27 @@ MATCHER_SOURCES = ("dco_stereo.cu", "kernels.cuh")   # the files that define the
 
 
 def source_digest() -> str:
-    """Digest of the matcher kernels' source files without their comments,
-    stamped into the ncu summaries under profiles/ (a summary of other code
-    is not used; a change of comments alone keeps the digest)."""
-    h = hashlib.sha256()
-    for f in MATCHER_SOURCES:
-        with open(os.path.join(ROOT, "paper_2203_02300_gb300", "csrc", f)) as fh:
-            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    """Digest of the matcher's device code and launch geometry without
+    comments, stamped into the ncu summaries under profiles/ (a summary of
+    other code is not used).  It covers kernels.cuh, the device part of
+    dco_stereo.cu (everything before its host section) and the geometry
+    functions that size the launches; changes of comments, includes or other
+    host code keep it."""
+    def strip(code: str) -> str:
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
         code = re.sub(r"//[^\n]*", "", code)
-        h.update("\n".join(l.rstrip() for l in code.splitlines() if l.strip()).encode())
+        return "\n".join(l.rstrip() for l in code.splitlines() if l.strip() and not l.startswith("#include"))
+    csrc = os.path.join(ROOT, "paper_2203_02300_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels.cuh")) as fh:
+        parts = [fh.read()]
+    with open(os.path.join(csrc, "dco_stereo.cu")) as fh:
+        cu = fh.read()
+    host = cu.index("// ====================================================================== host")
+    parts.append(cu[:host])
+    parts.append(cu[cu.index("struct HGeom {"):cu.index("// ---- TMA tile maps")])
+    h = hashlib.sha256()
+    for part in parts:
+        h.update(strip(part).encode())
     return h.hexdigest()[:16]
 
 

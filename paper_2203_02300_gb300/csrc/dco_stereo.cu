@@ -28,6 +28,7 @@
 #include "dco_stereo.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1423,9 +1424,6 @@ struct HGeom {
     dim3 grid;
 };
 
-// the other aggregation order: k_vcost walks columns (one chunk of rows per
-// block while it fits 32 warps of 32 rows), k_vagg<.., kRow> rows (the scan
-// range along x at most 512 columns, like k_vagg's rows)
 // Output positions per block of a first-pass line of n positions: the whole
 // line up to kHMaxLen, else 512 (want = 0); otherwise `want`, capped so that
 // a block's prefix range (chunk + 2 L1 halo) stays within kHMaxLen.
@@ -1437,6 +1435,9 @@ int first_pass_chunk(int n, int L1, int want)
     return c;
 }
 
+// the other aggregation order: k_vcost walks columns (one chunk of rows per
+// block while it fits 32 warps of 32 rows), k_vagg<.., kRow> rows (the scan
+// range along x at most 512 columns, like k_vagg's rows)
 HGeom vcost_geom(int W, int H, int dc, int L1, int want)
 {
     HGeom g{};
@@ -1923,7 +1924,10 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
 // padding reads the next group's first words (zeros past the last group).
 dco_status slice_map(dco_stereo *h, VArgs &a, int v, const uint32_t *slice, int W, int H, int dstride, bool row_scan)
 {
-    static int rank = 4;   // the encoder's answer for rank 4, kept for the process
+    // the encoder's answer for rank 4, kept for the process (serving lanes
+    // encode maps from several threads)
+    static std::atomic<int> rank_seen{4};
+    int rank = rank_seen.load(std::memory_order_relaxed);
     TmapEncode enc = tmap_encoder();
     if (!enc) {
         h->last_error = "cuTensorMapEncodeTiled is not available";
@@ -1939,7 +1943,10 @@ dco_status slice_map(dco_stereo *h, VArgs &a, int v, const uint32_t *slice, int 
         r = enc(&a.tm[v], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<uint32_t *>(slice), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) rank = 3;
+        if (r != CUDA_SUCCESS) {
+            rank = 3;
+            rank_seen.store(3, std::memory_order_relaxed);
+        }
     }
     if (rank == 3) {
         const cuuint64_t dims[3] = {(cuuint64_t)dstride, (cuuint64_t)W, (cuuint64_t)H};
