@@ -797,20 +797,62 @@ __device__ __forceinline__ void vcost_body(const HArgs &a, int bx, int by, int b
 // Horizontal pass of the parallax optimisation (Sect. 4.3, Eq. 4): block =
 // (row, group of 32 disparities), lane = disparity, local prefixes over warp
 // segments of 64 columns of the indicator [disp(x, y) == d] of the map being
-// voted on (-1 matches no d), then the output phase of the horizontal passes
-// (hagg_tail), so S_H holds the number of pixels of each horizontal segment
-// that vote for d.
+// voted on (-1 matches no d), then the output phase of the horizontal passes,
+// so S_H holds the number of pixels of each horizontal segment that vote for
+// d.  A local prefix counts at most 64 columns, so P keeps it in one byte
+// per disparity (32 bytes per column): a quarter of the 4-byte prefix rows
+// of the cost pass, so that more blocks fit an SM.
 struct HVSmem {
     int disp, arm, p, t, total;
     __host__ __device__ HVSmem(int len, int chunk, int nw)
     {
         disp = 0;
         arm = (len * 2 + 15) / 16 * 16;
-        p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
-        t = p + len * 128;
+        p = arm + (chunk + 3) / 4 * 16 + 32;    // one zero row in front: P[-1]
+        t = p + (len * 32 + 15) / 16 * 16;
         total = t + nw * 128;
     }
 };
+
+// The output phase of k_hvote: as hagg_out_quads, with byte prefixes (each
+// lane of a quarter-warp reads the four counts of its disparities 4j .. 4j + 3
+// as one word and widens them; unsigned wrap-around keeps the differences
+// exact once the segment offsets are added).
+template <int kSegLog>
+__device__ __forceinline__ void hvote_out_quads(const uint8_t *P, const uint32_t *OFF, const uchar4 *sarm,
+                                                int n_out, int base, uint32_t *o, size_t ds)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int l8 = lane & 7;
+    const uint32_t *P4 = reinterpret_cast<const uint32_t *>(P) + l8;   // rows of 8 words
+    const uint4 *F4 = reinterpret_cast<const uint4 *>(OFF) + l8;
+    uint4 *o4 = reinterpret_cast<uint4 *>(o) + l8;
+    const size_t ds4 = ds / 4;
+    auto column = [&](int i) -> uint4 {
+        const uchar4 am = sarm[i];
+        const int hi = base + i + am.y, lo = base + i - am.x - 1;   // lo >= -1
+        const uint32_t a = P4[hi * 8], b = P4[lo * 8];
+        uint4 v = make_uint4((a & 0xffu) - (b & 0xffu), ((a >> 8) & 0xffu) - ((b >> 8) & 0xffu),
+                             ((a >> 16) & 0xffu) - ((b >> 16) & 0xffu), (a >> 24) - (b >> 24));
+        const int sh = hi >> kSegLog, sl = max(lo, 0) >> kSegLog;
+        if (sh != sl) {   // the arm interval crosses segment boundaries
+            const uint4 fh = F4[sh * 8], fl = F4[sl * 8];
+            v.x += fh.x - fl.x;
+            v.y += fh.y - fl.y;
+            v.z += fh.z - fl.z;
+            v.w += fh.w - fl.w;
+        }
+        return v;
+    };
+    int i = 4 * warp + (lane >> 3);
+    const int step = 4 * nw;
+    for (; i + step < n_out; i += 2 * step) {
+        const uint4 v0 = column(i), v1 = column(i + step);
+        o4[(size_t)i * ds4] = v0;
+        o4[(size_t)(i + step) * ds4] = v1;
+    }
+    if (i < n_out) o4[(size_t)i * ds4] = column(i);
+}
 
 __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int bz)
 {
@@ -823,9 +865,9 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
     const HVSmem L(len, a.chunk, nw);
     int16_t *sd = reinterpret_cast<int16_t *>(smem_raw + L.disp);
     uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);
-    uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32], P[-1] = 0
+    uint8_t *P = smem_raw + L.p;                                   // [len][32] bytes, P[-1] = 0
     uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [nw][32]
-    if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
+    if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0;
     const int16_t *drow = a.disp + (size_t)y * W;
     const uchar4 *aref = a.arms + (size_t)y * W;
     for (int i = threadIdx.x; i < len; i += blockDim.x) sd[i] = drow[xa + i];
@@ -835,15 +877,23 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
     // ---- A: votes and local prefix of this warp's segment (lane = d)
     const int d = a.d0 + 32 * g + lane;
     const int sa = warp * kHSeg, sb = min(len, sa + kHSeg);   // relative to xa
+    static_assert(kHSeg <= 255, "k_hvote: local prefixes in one byte");
     uint32_t run = 0;
 #pragma unroll 8
     for (int x = sa; x < sb; x++) {
         run += sd[x] == d ? 1u : 0u;
-        P[x * 32 + lane] = run;
+        P[x * 32 + lane] = (uint8_t)run;
     }
     T[warp * 32 + lane] = run;
     __syncthreads();
-    hagg_tail<kHSegLog>(P, T, sarm, xe - xs, xs - xa, a.sh + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
+    // B: exclusive prefix of the segment totals (segment offsets), then C
+    uint32_t offs = 0;
+    for (int w = 0; w < warp; w++) offs += T[w * 32 + lane];
+    __syncthreads();
+    T[warp * 32 + lane] = offs;
+    __syncthreads();
+    hvote_out_quads<kHSegLog>(P, T, sarm, xe - xs, xs - xa, a.sh + ((size_t)y * W + xs) * a.dstride + g * 32,
+                              a.dstride);
 }
 
 // ------------------------------------------------------------------ k_vagg
