@@ -283,6 +283,21 @@ def test_vh_order_cost_volume(env):
     parity.check_volume(got, ref.vol_l, "volume view 0, order 1")
 
 
+def test_config5_full_frame(env):
+    # one 1920x1080 D=256 pair (32 planes, 200 discs, sigma 3) whole, against
+    # the FP64 oracle (about a billion FP64 evaluations on the host cores)
+    torch, binding, st = env
+    s = scenes.config_scene(5)
+    out, dl, dr, cl, cr = run_views(env, s.left, s.right, s.D)
+    ref = O.match(s.left, s.right, s.D)
+    what = "config 5 pair 0 (1920x1080 D=256) full frame"
+    parity.check_disparity(dl, ref.disp_l, ref.best_l, ref.second_l, what + " left disparity")
+    parity.check_disparity(dr, ref.disp_r, ref.best_r, ref.second_r, what + " right disparity")
+    parity.check_cost(cl, ref.best_l, dl, ref.disp_l, what + " left cost")
+    parity.check_cost(cr, ref.best_r, dr, ref.disp_r, what + " right cost")
+    parity.check_final(out, ref, what + " final map")
+
+
 def test_vh_order_config5_sampled_rows(env):
     # 1920x1080 D=256: k_vcost sums the 1080-row columns in chunks of 512
     # rows (rows 509..515 straddle the first boundary), k_vagg scans the
