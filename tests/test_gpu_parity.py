@@ -242,6 +242,15 @@ def test_vh_order_config1_full_parity(env):
     assert ((dl == gt) & ~s.occluded).sum() / (~s.occluded).sum() > 0.99
 
 
+@pytest.mark.parametrize("over", [dict(agg_order=1), dict(smooth_arms=1), dict(agg_order=1, smooth_arms=1)])
+def test_config2_variants_full_parity(env, over):
+    # the V-then-H order and the smoothed window on the whole 640x480 D=64
+    # frame of the metric's workload
+    torch, binding, st = env
+    s = scenes.config_scene(2)
+    full_check(env, s.left, s.right, s.D, binding.Params.default(**over), label=f"config 2 {over}")
+
+
 def test_vh_order_differs_from_hv_order(env):
     # the two regions differ wherever arms of neighbours differ: the costs
     # must not be equal everywhere (guards against a silent order-0 run)
