@@ -40,6 +40,21 @@
 
 namespace dco {
 
+// Programmatic dependent launch: every kernel of the paths is launched with
+// programmatic stream serialization, so the launch of a kernel overlaps the
+// end of the previous one in the stream.  Before touching global memory a
+// block waits until the previous grids have completed and their writes are
+// visible.  No block triggers its dependents early: blocks of the next
+// kernel parked on free SMs while a multi-pass run's last waves drain made
+// those runs slower (1920x1080 in passes of 32: 5.12 against 4.31 ms);
+// with the trigger at grid exit the launch latency alone is hidden
+// (640x480 D=64: 165 -> 156 us per pair, 320x240 D=32: 46 -> 36.5 us).
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+
 // ------------------------------------------------------------------ k_pack
 // RGB (3 bytes per pixel) -> packed 32-bit colour and the integer grey level
 // of the census, for both images; four pixels (12 bytes) per thread.
@@ -1176,6 +1191,7 @@ __device__ __forceinline__ void lr_body(const LrArgs &a, size_t i)
 // pixel (x, y) is the rounded mean (sum + 2) >> 2 of its 2x2 input block.
 __global__ void __launch_bounds__(256) k_down(const DownArgs a)
 {
+    pdl_enter();
     const int Wh = a.W / 2, Hh = a.H / 2;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= Wh || y >= Hh) return;
@@ -1192,6 +1208,7 @@ __global__ void __launch_bounds__(256) k_down(const DownArgs a)
 // ceil(W/2) x ceil(H/2) blocks.
 __global__ void __launch_bounds__(256) k_depth(const DepthArgs a)
 {
+    pdl_enter();
     const int hx = blockIdx.x * blockDim.x + threadIdx.x, hy = blockIdx.y;
     if (2 * hx >= a.W) return;
     const int Wh = a.W / 2;
@@ -1219,20 +1236,6 @@ struct Batch {
     int gx[N], gy[N]; // the pair's own grid is gx x gy x gz
     A p[N];
 };
-
-// Programmatic dependent launch: every batched kernel is launched with
-// programmatic stream serialization, so the launch of a kernel overlaps the
-// end of the previous one in the stream.  Before touching global memory a
-// block waits until the previous grids have completed and their writes are
-// visible.  No block triggers its dependents early: blocks of the next
-// kernel parked on free SMs while a multi-pass run's last waves drain made
-// those runs slower (1920x1080 in passes of 32: 5.12 against 4.31 ms);
-// with the trigger at grid exit the launch latency alone is hidden
-// (640x480 D=64: 165 -> 156 us per pair, 320x240 D=32: 46 -> 36.5 us).
-__device__ __forceinline__ void pdl_enter()
-{
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-}
 
 // launch with programmatic stream serialization (the kernel calls pdl_enter
 // before any global memory access)
@@ -2550,7 +2553,7 @@ dco_status dco_stereo_downscale(dco_stereo *h, const uint8_t *rgb, int W, int H,
     DownArgs da{};
     da.src[0] = rgb; da.dst[0] = out; da.W = W; da.H = H;
     ProfScope ps(h, s, "k_down");
-    k_down<<<dim3((unsigned)((W / 2 + 255) / 256), (unsigned)(H / 2), 1), 256, 0, s>>>(da);
+    launch_pdl(k_down, dim3((unsigned)((W / 2 + 255) / 256), (unsigned)(H / 2), 1), dim3(256), 0, s, da);
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
 }
@@ -2586,14 +2589,14 @@ dco_status dco_stereo_depth(dco_stereo *h, const uint8_t *left, const uint8_t *r
     j.out = disp_half_out ? disp_half_out : ws_ptr<int16_t>(h, 2 * img);
     {
         ProfScope ps(h, s, "k_down");
-        k_down<<<dim3((unsigned)((Wh + 255) / 256), (unsigned)Hh, 2), 256, 0, s>>>(da);
+        launch_pdl(k_down, dim3((unsigned)((Wh + 255) / 256), (unsigned)Hh, 2), dim3(256), 0, s, da);
         DCO_CUDA(h, cudaGetLastError());
     }
     if ((st = launch_jobs(h, p, dv, jobs, s)) != DCO_OK) return st;
     DepthArgs za{};
     za.disp = j.out; za.out = depth_out; za.W = W; za.H = H; za.fb = (float)(f_px * baseline);
     ProfScope ps(h, s, "k_depth");
-    k_depth<<<dim3((unsigned)(((W + 1) / 2 + 255) / 256), (unsigned)((H + 1) / 2)), 256, 0, s>>>(za);
+    launch_pdl(k_depth, dim3((unsigned)(((W + 1) / 2 + 255) / 256), (unsigned)((H + 1) / 2)), dim3(256), 0, s, za);
     DCO_CUDA(h, cudaGetLastError());
     return DCO_OK;
 }
