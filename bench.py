@@ -539,8 +539,10 @@ def vh_order_config2(torch, binding, st, L, R, D, dchunk, flush, dev, reps: int 
 def densify_full_size(torch, binding, st, flush, dev, W: int = 1280, H: int = 720, reps: int = 5):
     """Eq. 20 on a 1280x720 frame: the sparse depth of the quarter-size path,
     a depth contour where the ground truth jumps, texture weights from the
-    image gradient (M_fuse = 1).  Median time per solve, iterations, and the
-    two streaming kernels against their algorithmic bytes."""
+    image gradient (M_fuse = 1).  Median time per solve and iterations with
+    the one-launch solve (solver 0) and with two launches per iteration
+    (solver 1, whose two streaming kernels are set against their algorithmic
+    bytes)."""
     import numpy as np
     from paper_2203_02300_gb300 import scenes
     s = scenes.plane_scene(W, H, 128, 12, seed=scenes.seed_for(2, 950), drange=(4, 120), slanted=True,
@@ -556,41 +558,47 @@ def densify_full_size(torch, binding, st, flush, dev, W: int = 1280, H: int = 72
     mi = torch.from_numpy((gm / gm.max()).astype(np.float32)).to(dev)
     mf = torch.ones_like(mi)
     out = torch.empty_like(z)
-    p = binding.DenseParams.default()
     stream = torch.cuda.current_stream(dev)
-    st.densify(z, Bd, mf, mi, None, p, out=out)
-    ts = []
-    for _ in range(reps):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        st.densify(z, Bd, mf, mi, None, p, out=out)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        ts.append(a.elapsed_time(b))
-    iters, rel = st.densify_stats()
-    st.set_profiling(True)
-    st.profile_reset()
-    st.densify(z, Bd, mf, mi, None, p, out=out)
-    torch.cuda.synchronize(dev)
-    prof = st.profile()
-    st.set_profiling(False)
     pk, _ = peaks()
     n = W * H
     alg = {"k_dn_ap": 4 * n * 7, "k_dn_upd": 4 * n * 8}   # ap: z, p, wr, wd, diag in; p, Ap out. upd: x, p, r, Ap, diag in; x, r, z out
-    kern = {}
-    for k, (cnt, ms) in prof.items():
-        avg = ms / cnt * 1e3
-        e = {"launches": cnt, "avg_us": round(avg, 3)}
-        if k in alg:
-            gbs = alg[k] / (avg * 1e-6) / 1e9
-            e.update(achieved_gbs=round(gbs, 1), frac_hbm=round(gbs / pk["hbm_gbs"], 4))
-        kern[k] = e
-    med = statistics.median(ts)
-    return {"size": f"{W}x{H}", "sparse_fraction": float((z > 0).float().mean().item()),
-            "iterations": iters, "rel_residual": rel, "tol": float(p.tol), "ms_per_solve": round(med, 3),
-            "us_per_iteration": round(1e3 * med / max(iters, 1), 2), "kernels": kern}
+    res = {"size": f"{W}x{H}", "sparse_fraction": float((z > 0).float().mean().item())}
+    for solver in (0, 1):
+        p = binding.DenseParams.default(solver=solver)
+        st.densify(z, Bd, mf, mi, None, p, out=out)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.densify(z, Bd, mf, mi, None, p, out=out)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        iters, rel = st.densify_stats()
+        st.set_profiling(True)
+        st.profile_reset()
+        st.densify(z, Bd, mf, mi, None, p, out=out)
+        torch.cuda.synchronize(dev)
+        prof = st.profile()
+        st.set_profiling(False)
+        kern = {}
+        for k, (cnt, ms) in prof.items():
+            avg = ms / cnt * 1e3
+            e = {"launches": cnt, "avg_us": round(avg, 3)}
+            if k in alg:
+                gbs = alg[k] / (avg * 1e-6) / 1e9
+                e.update(achieved_gbs=round(gbs, 1), frac_hbm=round(gbs / pk["hbm_gbs"], 4))
+            kern[k] = e
+        med = statistics.median(ts)
+        r = {"iterations": iters, "rel_residual": rel, "tol": float(p.tol), "ms_per_solve": round(med, 3),
+             "us_per_iteration": round(1e3 * med / max(iters, 1), 2), "kernels": kern}
+        if solver == 0:
+            res.update(r)
+        else:
+            res["per_iteration_launches"] = r
+    return res
 
 
 # ------------------------------------------- quarter size + depth (Sect. 4.4)

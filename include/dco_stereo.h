@@ -281,6 +281,11 @@ typedef struct {
     float lambda_s2;  /* 0.02 */
     float tol;        /* 1e-5 */
     int max_iters;    /* 4000 */
+    int solver;       /* 0: the whole solve in one cooperative launch when
+                         every block's share of the pixels fits one block
+                         (about 0.93 M pixels on 152 multiprocessors), else
+                         two launches per iteration; 1: always two launches
+                         per iteration.  Same iterations and stopping rule. */
 } dco_dense_params;
 
 dco_status dco_dense_params_default(dco_dense_params *p);
@@ -292,9 +297,12 @@ dco_status dco_dense_params_default(dco_dense_params *p);
  * magnitude and the [0, 1]-normalised Canny intensity of Eq. 17, or NULL (0).
  * d_pre: device W*H float, the previous frame's depth, or NULL (no stability
  * term).  d_out: device W*H float.  p = NULL uses the defaults.  The call
- * waits for the solve (it reads a convergence flag between batches of
- * iterations); dco_stereo_densify_stats gives the iterations run and the
- * final relative residual.  Needs 36 bytes per pixel of workspace.
+ * waits for the solve (with solver 1 it reads a convergence flag between
+ * batches of iterations); dco_stereo_densify_stats gives the iterations run
+ * and the final relative residual.  Needs 36 bytes per pixel of workspace.
+ * DCO_ETIMEOUT if a grid barrier of the one-launch solve gave up (its waits
+ * are bounded); the map is then not a solution.  The call cannot be
+ * captured in a CUDA graph (DCO_EINVAL under capture).
  */
 dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_t *contour, const float *m_fuse,
                               const float *m_int, const float *d_pre, int W, int H, const dco_dense_params *p,

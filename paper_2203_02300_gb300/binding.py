@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
 class DenseParams(ctypes.Structure):
     """dco_dense_params; defaults from dco_dense_params_default()."""
     _fields_ = [("lambda_d", c_float), ("lambda_s", c_float), ("lambda_s2", c_float), ("tol", c_float),
-                ("max_iters", c_int)]
+                ("max_iters", c_int), ("solver", c_int)]
 
     @classmethod
     def default(cls, **over) -> "DenseParams":

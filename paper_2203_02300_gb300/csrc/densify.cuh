@@ -6,7 +6,9 @@
 // gradients with a Jacobi preconditioner, matrix free.  Included by
 // dco_stereo.cu after the handle helpers.
 //
-// Per iteration two launches:
+// The whole solve is one cooperative launch (k_dn_solve) when every block's
+// share of the pixels fits its registers and shared memory; otherwise (and
+// with dco_dense_params.solver = 1) two launches per iteration:
 //   k_dn_ap   p_new = z + beta p_old (both buffers kept: neighbours read the
 //             old one) and Ap = A p_new; alpha = r.z / p.Ap;
 //   k_dn_upd  x += alpha p, r -= alpha Ap, z = r / diag; beta = r.z / previous r.z.
@@ -26,6 +28,8 @@ struct DnScalars {
     double rz, pap, rr, bb, alpha, beta;
     int done, iters;
     unsigned count;   // blocks of the current launch that have written their partials
+    unsigned bar;     // grid barrier of k_dn_solve (zeroed by k_dn_init)
+    int lost;         // k_dn_solve gave up on a grid barrier
 };
 
 struct DnArgs {
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_init(const DnArgs a)
         sc->beta = 0.0;
         sc->iters = 0;
         sc->done = !(t0 > 0.0) || !(t1 > 0.0);
+        sc->bar = 0u;
+        sc->lost = 0;
     }
 }
 
@@ -259,6 +265,357 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_resid(const DnArgs a)
     }
 }
 
+// ---------------------------------------------------------- k_dn_solve
+// The whole CG loop in one cooperative launch.  Block b owns the pixels
+// [s_b, e_b) of the row-major image (an equal share); thread t the pixels
+// s_b + t + k * blockDim.x, k < kDnPx, whose x, r, z, p and Ap stay in
+// registers for the whole solve.  Shared memory holds the diagonal, the
+// block's weights over [s_b - W, e_b), p over [s_b - W, e_b + W) for the
+// stencil, and p of the two halo bands (the W pixels before and after the
+// share), which every
+// block forms itself from the owners' z (exchanged through global memory)
+// and the common beta, so an iteration needs two grid barriers: one per dot
+// product.  Every block adds the blocks' partial sums in the same fixed
+// order, so all blocks take the same alpha, beta and stopping decisions and
+// the result does not depend on timing.  The residual replacement every
+// kDnIters iterations (in double-float arithmetic here, in double there) and
+// the convergence test on it follow the multi-launch path.  A grid barrier
+// that does not complete within kDnWaitLimit polls sets sc->lost and ends
+// the solve in every block.
+constexpr int kDnSolveThreads = 1024;
+constexpr int kDnPx = 6;                  // pixels per thread
+constexpr int kDnIters = 16;              // iterations between residual replacements (even)
+constexpr int kDnWaitLimit = 1 << 22;     // polls of one grid barrier before the solve gives up
+constexpr int kDnHaloRound = 3;           // halo loads a thread issues together
+
+struct DnSolveArgs {
+    DnArgs a;
+    double *part;     // [2][nblocks][2] block partials, alternating between reductions
+    int max_iters;
+};
+
+__device__ __forceinline__ unsigned dn_ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier over a co-resident grid: every block adds 1 to a counter
+// that starts at 0 for the solve (no reply awaited), and waits until it
+// reaches the block's running target (nblocks per barrier passed).  False
+// (in every thread) if the target was not seen within `limit` polls.
+__device__ __forceinline__ bool dn_grid_sync(unsigned *bar, unsigned &target, int limit)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(bar) : "memory");
+        int ok = 0;
+        for (int i = 0; i < limit; i++) {
+            if ((int)(dn_ld_acquire(bar) - target) >= 0) { ok = 1; break; }
+            __nanosleep(32);
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Sums of (v0, v1) over the grid: FP32 warp sums, a double block sum in
+// partial buffer `red & 1`, the grid barrier, then every block adds the
+// blocks' sums in one fixed order.  False if the barrier was given up.
+__device__ __forceinline__ bool dn_allreduce(float v0, float v1, const DnSolveArgs &s, int red, unsigned &target,
+                                             double &t0, double &t1)
+{
+    __shared__ double s0[kDnSolveThreads / 32], s1[kDnSolveThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { s0[w] = v0; s1[w] = v1; }
+    __syncthreads();
+    double *part = s.part + (size_t)(red & 1) * gridDim.x * 2;
+    if (w == 0) {   // the warps' sums in a fixed tree
+        double u0 = l < nw ? s0[l] : 0.0, u1 = l < nw ? s1[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 += __shfl_down_sync(0xffffffffu, u0, o);
+            u1 += __shfl_down_sync(0xffffffffu, u1, o);
+        }
+        if (l == 0) {
+            part[2 * blockIdx.x] = u0;
+            part[2 * blockIdx.x + 1] = u1;
+        }
+    }
+    if (!dn_grid_sync(&s.a.sc->bar, target, kDnWaitLimit)) return false;
+    if (w == 0) {
+        // lane l adds blocks l, l + 32, ...: the loads of a round of eight are
+        // issued together (one L2 latency per 256 blocks)
+        double u0 = 0.0, u1 = 0.0;
+        const double2 *pp = reinterpret_cast<const double2 *>(part);
+        for (int k0 = 0; k0 < (int)gridDim.x; k0 += 256) {
+            double2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int k = k0 + l + 32 * q;
+                v[q] = k < (int)gridDim.x ? __ldcg(pp + k) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                u0 += v[q].x;
+                u1 += v[q].y;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 += __shfl_down_sync(0xffffffffu, u0, o);
+            u1 += __shfl_down_sync(0xffffffffu, u1, o);
+        }
+        if (l == 0) { s0[0] = u0; s1[0] = u1; }
+    }
+    __syncthreads();
+    t0 = s0[0];
+    t1 = s1[0];
+    __syncthreads();   // s0, s1 are rewritten by the next reduction
+    return true;
+}
+
+// Double-float arithmetic (an unevaluated sum hi + lo of two FP32 numbers,
+// about 44 significant bits) for the residual replacement: exact products by
+// FMA and error-free sums (Knuth's two-sum), FP32 instructions only (the
+// part's FP64 rate is low).
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df df_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return df{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df x, df y)
+{
+    const df s = df_two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    const float h = __fadd_rn(s.hi, e);
+    return df{h, __fsub_rn(e, __fsub_rn(h, s.hi))};
+}
+__device__ __forceinline__ df df_scale(df x, float c)   // x * c
+{
+    const df p = df_prod(x.hi, c);
+    const float e = __fmaf_rn(x.lo, c, p.lo);
+    const float h = __fadd_rn(p.hi, e);
+    return df{h, __fsub_rn(e, __fsub_rn(h, p.hi))};
+}
+
+// shared-memory floats of a block owning `len` pixels of rows W wide
+__host__ __device__ inline size_t dn_solve_smem_floats(long len, int W) { return 4 * (size_t)len + 6 * (size_t)W; }
+
+__global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_constant__ DnSolveArgs s)
+{
+    extern __shared__ float dsm[];
+    const DnArgs &a = s.a;
+    const long n = (long)a.W * a.H;
+    const int W = a.W, nb = gridDim.x, tid = threadIdx.x, nt = blockDim.x;
+    const long s0 = n * blockIdx.x / nb, e0 = n * (blockIdx.x + 1) / nb;
+    const int len = (int)(e0 - s0);
+    // PS: p (x in the residual replacement) over [s0 - W, e0 + W), index i - s0 + W;
+    // WR, WD: weights over [s0 - W, e0), same index; PH: p of the halo bands;
+    // DG: the diagonal of the share, index i - s0
+    float *PS = dsm, *WR = PS + len + 2 * W, *WD = WR + len + W, *PH = WD + len + W, *DG = PH + 2 * W;
+    const float ls2 = 2.0f * a.lambda_s;
+    auto halo_pixel = [&](int k) -> long { return k < W ? s0 - W + k : e0 + (k - W); };   // k < 2 W
+    auto halo_slot = [&](int k) -> int { return k < W ? k : len + W + (k - W); };         // its PS index
+    for (int k = tid; k < len + W; k += nt) {
+        const long i = s0 - W + k;
+        WR[k] = i >= 0 ? a.wr[i] : 0.0f;
+        WD[k] = i >= 0 ? a.wd[i] : 0.0f;
+    }
+    for (int k = tid; k < 2 * W; k += nt) PH[k] = 0.0f;
+    for (int k = tid; k < len; k += nt) DG[k] = a.dg[s0 + k];
+    float x[kDnPx], r[kDnPx], z[kDnPx], p[kDnPx], ap[kDnPx];
+#pragma unroll
+    for (int k = 0; k < kDnPx; k++) {
+        const int o = tid + k * nt;
+        const bool v = o < len;
+        x[k] = v ? a.x[s0 + o] : 0.0f;
+        r[k] = v ? a.r[s0 + o] : 0.0f;
+        z[k] = v ? a.z[s0 + o] : 0.0f;
+        p[k] = 0.0f;
+        ap[k] = 0.0f;
+    }
+    // o is a boundary pixel (its z and x are read by a neighbouring block)
+    auto edge = [&](int o) { return o < W || o >= len - W; };
+    // The scalars live in thread 0, which alone does their FP64 arithmetic
+    // (the part's FP64 rate is low), and reach the block through shared memory.
+    __shared__ float s_fa, s_fb;
+    __shared__ int s_done;
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    int iters = 0;
+    if (tid == 0) {
+        rz = a.sc->rz;
+        rr = a.sc->rr;
+        bb = a.sc->bb;
+        s_done = a.sc->done;
+        s_fb = 0.0f;
+    }
+    __syncthreads();
+    int done = s_done, red = 0;
+    unsigned target = 0;   // grid barrier count this block has passed, times the blocks
+    bool ok = true;
+    for (int it = 0; it < s.max_iters && !done; it++) {
+        // ---- p = z + beta p (own pixels and the halo bands), Ap = A p, p.Ap
+        const float fb = s_fb;
+#pragma unroll
+        for (int k = 0; k < kDnPx; k++) {
+            const int o = tid + k * nt;
+            p[k] = __fmaf_rn(fb, p[k], z[k]);
+            if (o < len) PS[W + o] = p[k];
+        }
+        for (int k0 = 0; k0 < 2 * W; k0 += kDnHaloRound * nt) {   // the owners' z, one L2 latency per round
+            float zj[kDnHaloRound];
+#pragma unroll
+            for (int u = 0; u < kDnHaloRound; u++) {
+                const int k = k0 + tid + u * nt;
+                const long j = halo_pixel(k);
+                zj[u] = k < 2 * W && j >= 0 && j < n ? __ldcg(a.z + j) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kDnHaloRound; u++) {
+                const int k = k0 + tid + u * nt;
+                if (k < 2 * W) {
+                    PH[k] = __fmaf_rn(fb, PH[k], zj[u]);
+                    PS[halo_slot(k)] = PH[k];
+                }
+            }
+        }
+        __syncthreads();
+        float pap = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kDnPx; k++) {
+            const int L = W + tid + k * nt;
+            if (L - W < len) {
+                float nbv = 0.0f;
+                nbv += WR[L] * PS[L + 1];
+                nbv += WR[L - 1] * PS[L - 1];
+                nbv += WD[L] * PS[L + W];
+                nbv += WD[L - W] * PS[L - W];
+                ap[k] = DG[L - W] * p[k] - ls2 * nbv;
+                pap += p[k] * ap[k];
+            }
+        }
+        double t0, t1;
+        ok = dn_allreduce(pap, 0.0f, s, red++, target, t0, t1);
+        if (!ok) break;
+        if (tid == 0) {
+            if (!(t0 > 0.0)) s_done = 1;   // no direction left (solved, or breakdown)
+            else s_fa = (float)rz / (float)t0;   // used in FP32: the FP32 quotient
+        }
+        __syncthreads();
+        if (s_done) { done = 1; break; }
+        const float fa = s_fa;
+        // ---- x += alpha p, r -= alpha Ap, z = r / diag; r.z, r.r
+        float rzp = 0.0f, rrp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kDnPx; k++) {
+            const int o = tid + k * nt;
+            if (o < len) {
+                x[k] += fa * p[k];
+                r[k] -= fa * ap[k];
+                const float d = DG[o];
+                z[k] = d > 0.0f ? r[k] / d : 0.0f;
+                rzp += r[k] * z[k];
+                rrp += r[k] * r[k];
+                if (edge(o)) {
+                    a.z[s0 + o] = z[k];
+                    a.x[s0 + o] = x[k];
+                }
+            }
+        }
+        ok = dn_allreduce(rzp, rrp, s, red++, target, t0, t1);
+        if (!ok) break;
+        if (tid == 0) {
+            s_fb = rz > 0.0 ? (float)t0 / (float)rz : 0.0f;   // beta, used in FP32
+            rz = t0;
+            rr = t1;
+            iters++;
+            if (!(t0 > 0.0)) s_done = 1;   // r = 0: solved
+        }
+        __syncthreads();
+        if (s_done) { done = 1; break; }
+        if ((it + 1) % kDnIters != 0 && it + 1 != s.max_iters) continue;
+        // ---- residual replacement: r = b - A x in double, z = r / diag
+#pragma unroll
+        for (int k = 0; k < kDnPx; k++) {
+            const int o = tid + k * nt;
+            if (o < len) PS[W + o] = x[k];
+        }
+        for (int k0 = 0; k0 < 2 * W; k0 += kDnHaloRound * nt) {
+            float xj[kDnHaloRound];
+#pragma unroll
+            for (int u = 0; u < kDnHaloRound; u++) {
+                const int k = k0 + tid + u * nt;
+                const long j = halo_pixel(k);
+                xj[u] = k < 2 * W && j >= 0 && j < n ? __ldcg(a.x + j) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kDnHaloRound; u++) {
+                const int k = k0 + tid + u * nt;
+                if (k < 2 * W) PS[halo_slot(k)] = xj[u];
+            }
+        }
+        __syncthreads();
+        rzp = 0.0f;
+        rrp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kDnPx; k++) {
+            const int L = W + tid + k * nt, o = L - W;
+            if (o < len) {
+                df nb = df_prod(WR[L], PS[L + 1]);
+                nb = df_add(nb, df_prod(WR[L - 1], PS[L - 1]));
+                nb = df_add(nb, df_prod(WD[L], PS[L + W]));
+                nb = df_add(nb, df_prod(WD[L - W], PS[L - W]));
+                const float d = DG[o];
+                df rd = df_add(df_scale(nb, ls2), df_prod(-d, x[k]));
+                rd = df_add(rd, df{a.b[s0 + o], 0.0f});
+                r[k] = __fadd_rn(rd.hi, rd.lo);
+                z[k] = d > 0.0f ? r[k] / d : 0.0f;
+                rzp += r[k] * z[k];
+                rrp += r[k] * r[k];
+                if (edge(o)) a.z[s0 + o] = z[k];
+            }
+        }
+        ok = dn_allreduce(rzp, rrp, s, red++, target, t0, t1);
+        if (!ok) break;
+        if (tid == 0) {
+            rz = t0;
+            rr = t1;
+            if (t1 <= a.tol2 * bb || !(t0 > 0.0)) s_done = 1;
+        }
+        __syncthreads();
+        done = s_done;
+    }
+#pragma unroll
+    for (int k = 0; k < kDnPx; k++) {
+        const int o = tid + k * nt;
+        if (o < len) a.x[s0 + o] = x[k];
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        a.sc->rz = rz;
+        a.sc->rr = rr;
+        a.sc->iters = iters;
+        a.sc->done = s_done;
+        if (!ok) a.sc->lost = 1;
+    }
+}
+
 }  // namespace dco
 
 // ------------------------------------------------------------- C ABI
@@ -274,6 +631,7 @@ dco_status dco_dense_params_default(dco_dense_params *p)
     p->lambda_s2 = 0.02f;
     p->tol = 1e-5f;
     p->max_iters = 4000;
+    p->solver = 0;
     return DCO_OK;
 }
 
@@ -286,7 +644,7 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
     if (pin) p = *pin;
     else dco_dense_params_default(&p);
     if (!(p.lambda_d >= 0.f) || !(p.lambda_s >= 0.f) || !(p.lambda_s2 >= 0.f) || !(p.tol > 0.f) ||
-        p.max_iters < 0 || p.max_iters > 1000000)
+        p.max_iters < 0 || p.max_iters > 1000000 || p.solver < 0 || p.solver > 1)
         return DCO_EINVAL;
     DCO_CUDA(h, enter_device(h));
     cudaStream_t s = (cudaStream_t)stream;
@@ -300,10 +658,31 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
     // grid-stride kernels: at most 8 resident blocks per multiprocessor
     int nsm = 0;
     DCO_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int nblk = (int)std::min<size_t>((n + kDnBlock - 1) / kDnBlock, (size_t)std::max(nsm, 1) * 8);
-    // workspace: r, z, p0, p1, Ap, wr, wd, diag, b; block partials; scalars
+    nsm = std::max(nsm, 1);
+    const int nblk = (int)std::min<size_t>((n + kDnBlock - 1) / kDnBlock, (size_t)nsm * 8);
+    // the one-launch solve: one block per multiprocessor (fewer for small
+    // images), each share within kDnPx pixels per thread and the shared memory
+    // of one block; cooperative launch, so every block is resident
+    const int sblk = (int)std::min<size_t>((n + kDnSolveThreads - 1) / kDnSolveThreads, (size_t)nsm);
+    const size_t share = (n + sblk - 1) / sblk;
+    const size_t ssmem = sizeof(float) * dn_solve_smem_floats((long)share, W);
+    bool one_launch = p.solver == 0 && share <= (size_t)kDnSolveThreads * kDnPx && ssmem <= (size_t)200 * 1024;
+    if (one_launch) {
+        int coop = 0;
+        DCO_CUDA(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+        one_launch = coop != 0;
+    }
+    if (one_launch) {
+        dco_status st = opt_in_smem(h, (const void *)k_dn_solve, ssmem);
+        if (st != DCO_OK) return st;
+        int per_sm = 0;
+        DCO_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dn_solve, kDnSolveThreads, ssmem));
+        one_launch = per_sm >= 1;
+    }
+    // workspace: r, z, p0, p1, Ap, wr, wd, diag, b; block partials (two
+    // buffers of the one-launch solve); scalars
     const size_t fl = align_up(4 * n);
-    const size_t off_part = 9 * fl, off_sc = off_part + align_up(16 * (size_t)nblk);
+    const size_t off_part = 9 * fl, off_sc = off_part + align_up(16 * (size_t)std::max(nblk, 2 * sblk));
     dco_status st = ensure_ws(h, off_sc + align_up(sizeof(DnScalars)));
     if (st != DCO_OK) return st;
     if (!h->dn_pin) {
@@ -331,13 +710,36 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
         launch_pdl(k_dn_init, dim3(nblk), dim3(kDnBlock), 0, s, a);
     }
     DCO_CUDA(h, cudaGetLastError());
+    if (one_launch) {
+        DnSolveArgs sa;
+        std::memset(&sa, 0, sizeof sa);
+        sa.a = a;
+        sa.part = a.part;
+        sa.max_iters = p.max_iters;
+        void *args[] = {&sa};
+        {
+            ProfScope ps(h, s, "k_dn_solve");
+            DCO_CUDA(h, cudaLaunchCooperativeKernel((const void *)k_dn_solve, dim3(sblk), dim3(kDnSolveThreads), args,
+                                                    ssmem, s));
+        }
+        h->launches += 1;
+        DnScalars sc{};
+        DCO_CUDA(h, cudaMemcpyAsync(&sc, a.sc, sizeof sc, cudaMemcpyDeviceToHost, s));
+        DCO_CUDA(h, cudaStreamSynchronize(s));
+        h->dn_iters = sc.iters;
+        h->dn_relres = sc.bb > 0.0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+        if (sc.lost) {
+            h->last_error = "densify: a grid barrier of the solve did not complete";
+            return DCO_ETIMEOUT;
+        }
+        return DCO_OK;
+    }
     // Iterations run in batches of kDnIters, each closed by the residual
     // replacement, the true-residual test and a copy of the (sticky) done
     // flag to pinned memory.  A batch is one CUDA graph launch (captured once
     // per argument set on a private stream; per-kernel profiling uses plain
     // launches instead); the host keeps one batch queued ahead and stops
     // enqueuing once the flag of an earlier batch reads 1.
-    constexpr int kDnIters = 16;   // even: buffer parity repeats per batch
     auto enqueue = [&](cudaStream_t q, int it0, int m, bool prof) -> cudaError_t {
         for (int k = 0; k < m; k++) {
             const int it = it0 + k;

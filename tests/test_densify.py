@@ -58,11 +58,13 @@ def _true_relres(x, ds, B, mf, mi, dp, p):
 # The attainable residual relative to ||b|| is bounded by the FP32 storage of
 # x: about 2^-24 * |A x| per pixel against b, which is nonzero only where data
 # exist, so sparser data need a larger tol (2 % data: ~5e-6 at best).
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("H,W,frac,tol", [(30, 40, 0.1, 1e-6), (61, 97, 0.3, 1e-6), (17, 230, 0.02, 2e-5)])
-def test_densify_equals_the_direct_solve(env, H, W, frac, tol):
+def test_densify_equals_the_direct_solve(env, H, W, frac, tol, solver):
+    # solver 0: one cooperative launch for the solve; 1: two launches per iteration
     rng = np.random.default_rng(H * W)
     ds, B, mf, mi, dp = _inputs(rng, H, W, frac)
-    x, (iters, rel) = _solve(env, ds, B, mf, mi, dp, tol=tol, max_iters=20000)
+    x, (iters, rel) = _solve(env, ds, B, mf, mi, dp, tol=tol, max_iters=20000, solver=solver)
     p = DN.DenseParams()
     want = DN.densify(ds.astype(np.float64), B, mf, mi, dp.astype(np.float64), p)
     assert 0 < iters < 20000 and rel <= tol
@@ -82,10 +84,11 @@ def test_densify_single_anchor_and_contour_split(env):
     assert np.allclose(x[:, :5], 1.0, rtol=1e-5) and np.allclose(x[:, 5:], 4.0, rtol=1e-5)
 
 
-def test_densify_without_smoothness_is_the_data(env):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_densify_without_smoothness_is_the_data(env, solver):
     rng = np.random.default_rng(3)
     ds, B, mf, mi, dp = _inputs(rng, 20, 30, 0.5)
-    x, (iters, _) = _solve(env, ds, B, mf, mi, dp, lambda_s=0.0, tol=1e-7)
+    x, (iters, _) = _solve(env, ds, B, mf, mi, dp, lambda_s=0.0, tol=1e-7, solver=solver)
     ws, wt = (ds > 0) * 0.8, (dp > 0) * 0.02
     want = np.where(ws + wt > 0, (ws * ds + wt * dp) / np.where(ws + wt > 0, ws + wt, 1), 0.0)
     assert np.allclose(x, want, rtol=1e-6, atol=0) and iters <= 16   # exact after one step; checked per batch of 16
@@ -96,6 +99,26 @@ def test_densify_undetermined_regions_stay_zero(env):
     s = np.zeros((6, 10), np.float32); s[:, 5:] = 1.0
     x, _ = _solve(env, ds, None, s, np.ones((6, 10), np.float32), None, tol=1e-7)
     assert np.allclose(x[:, :6], 1.0, rtol=1e-5) and (x[:, 6:] == 0).all()
+
+
+def test_densify_one_launch_and_per_iteration_launches_agree(env):
+    # a frame that spreads over every multiprocessor (several blocks, halo
+    # bands crossing rows): both solvers reach the tolerance, stop within one
+    # batch of iterations of each other and agree with the direct solve
+    rng = np.random.default_rng(11)
+    H, W = 270, 480
+    ds, B, mf, mi, dp = _inputs(rng, H, W, 0.3)
+    x0, (i0, r0) = _solve(env, ds, B, mf, mi, dp, tol=1e-6, max_iters=20000, solver=0)
+    x1, (i1, r1) = _solve(env, ds, B, mf, mi, dp, tol=1e-6, max_iters=20000, solver=1)
+    p = DN.DenseParams()
+    want = DN.densify(ds.astype(np.float64), B, mf, mi, dp.astype(np.float64), p)
+    for name, x, rel in (("one launch", x0, r0), ("per-iteration launches", x1, r1)):
+        assert rel <= 1e-6, name
+        assert _true_relres(x, ds, B, mf, mi, dp, p) <= 2.5e-6, name
+        err = np.abs(x - want).max() / np.abs(want).max()
+        assert err <= 1e-3, (name, err)
+        assert (x[want == 0] == 0).all(), name
+    assert abs(i0 - i1) <= 16, (i0, i1)
 
 
 def test_densify_a_stereo_depth_map(env):
@@ -122,7 +145,7 @@ def test_densify_a_stereo_depth_map(env):
 def test_densify_rejects_bad_arguments(env):
     torch, binding, st = env
     d = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
-    for over in (dict(tol=0.0), dict(lambda_s=-1.0), dict(max_iters=-1)):
+    for over in (dict(tol=0.0), dict(lambda_s=-1.0), dict(max_iters=-1), dict(solver=2), dict(solver=-1)):
         with pytest.raises(binding.DcoError) as e:
             st.densify(d, params=binding.DenseParams.default(**over))
         assert e.value.code == binding.DCO_EINVAL
