@@ -325,64 +325,6 @@ __device__ __forceinline__ bool dn_grid_sync(unsigned *bar, unsigned &target, in
     return ok_s != 0;
 }
 
-// Sums of (v0, v1) over the grid: FP32 warp sums, a double block sum in
-// partial buffer `red & 1`, the grid barrier, then every block adds the
-// blocks' sums in one fixed order.  False if the barrier was given up.
-__device__ __forceinline__ bool dn_allreduce(float v0, float v1, const DnSolveArgs &s, int red, unsigned &target,
-                                             double &t0, double &t1)
-{
-    __shared__ double s0[kDnSolveThreads / 32], s1[kDnSolveThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_down_sync(0xffffffffu, v0, o);
-        v1 += __shfl_down_sync(0xffffffffu, v1, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) { s0[w] = v0; s1[w] = v1; }
-    __syncthreads();
-    double *part = s.part + (size_t)(red & 1) * gridDim.x * 2;
-    if (w == 0) {   // the warps' sums in a fixed tree
-        double u0 = l < nw ? s0[l] : 0.0, u1 = l < nw ? s1[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            u0 += __shfl_down_sync(0xffffffffu, u0, o);
-            u1 += __shfl_down_sync(0xffffffffu, u1, o);
-        }
-        if (l == 0) {
-            part[2 * blockIdx.x] = u0;
-            part[2 * blockIdx.x + 1] = u1;
-        }
-    }
-    if (!dn_grid_sync(&s.a.sc->bar, target, kDnWaitLimit)) return false;
-    if (w == 0) {
-        // lane l adds blocks l, l + 32, ...: the loads of a round of eight are
-        // issued together (one L2 latency per 256 blocks)
-        double u0 = 0.0, u1 = 0.0;
-        const double2 *pp = reinterpret_cast<const double2 *>(part);
-        for (int k0 = 0; k0 < (int)gridDim.x; k0 += 256) {
-            double2 v[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int k = k0 + l + 32 * q;
-                v[q] = k < (int)gridDim.x ? __ldcg(pp + k) : make_double2(0.0, 0.0);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                u0 += v[q].x;
-                u1 += v[q].y;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            u0 += __shfl_down_sync(0xffffffffu, u0, o);
-            u1 += __shfl_down_sync(0xffffffffu, u1, o);
-        }
-        if (l == 0) { s0[0] = u0; s1[0] = u1; }
-    }
-    __syncthreads();
-    t0 = s0[0];
-    t1 = s1[0];
-    __syncthreads();   // s0, s1 are rewritten by the next reduction
-    return true;
-}
-
 // Double-float arithmetic (an unevaluated sum hi + lo of two FP32 numbers,
 // about 44 significant bits) for the residual replacement: exact products by
 // FMA and error-free sums (Knuth's two-sum), FP32 instructions only (the
@@ -413,6 +355,65 @@ __device__ __forceinline__ df df_scale(df x, float c)   // x * c
     const float e = __fmaf_rn(x.lo, c, p.lo);
     const float h = __fadd_rn(p.hi, e);
     return df{h, __fsub_rn(e, __fsub_rn(h, p.hi))};
+}
+
+// Sums of (v0, v1) over the grid: FP32 warp sums, the block's sum of its
+// warps in double-float (a fixed tree in warp 0) in partial buffer `red & 1`,
+// the grid barrier, then every block adds the blocks' sums in one fixed order
+// (double-float), and thread 0 passes the two totals to `decide`, whose
+// shared-memory results the block reads after this call.  False if the
+// barrier was given up (decide is then not called).
+__device__ __forceinline__ df df_shfl_down(df x, int o)
+{
+    return df{__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+}
+template <class Decide>
+__device__ __forceinline__ bool dn_allreduce(float v0, float v1, const DnSolveArgs &s, int red, unsigned &target,
+                                             Decide decide)
+{
+    __shared__ float s0[kDnSolveThreads / 32], s1[kDnSolveThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { s0[w] = v0; s1[w] = v1; }
+    __syncthreads();
+    float4 *part = reinterpret_cast<float4 *>(s.part) + (size_t)(red & 1) * gridDim.x;
+    if (w == 0) {
+        df u0{l < nw ? s0[l] : 0.0f, 0.0f}, u1{l < nw ? s1[l] : 0.0f, 0.0f};
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 = df_add(u0, df_shfl_down(u0, o));
+            u1 = df_add(u1, df_shfl_down(u1, o));
+        }
+        if (l == 0) part[blockIdx.x] = make_float4(u0.hi, u0.lo, u1.hi, u1.lo);
+    }
+    if (!dn_grid_sync(&s.a.sc->bar, target, kDnWaitLimit)) return false;
+    if (w == 0) {
+        // lane l adds blocks l, l + 32, ...: the loads of a round of eight are
+        // issued together (one L2 latency per 256 blocks)
+        df u0{0.0f, 0.0f}, u1{0.0f, 0.0f};
+        for (int k0 = 0; k0 < (int)gridDim.x; k0 += 256) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int k = k0 + l + 32 * q;
+                v[q] = k < (int)gridDim.x ? __ldcg(part + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                u0 = df_add(u0, df{v[q].x, v[q].y});
+                u1 = df_add(u1, df{v[q].z, v[q].w});
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 = df_add(u0, df_shfl_down(u0, o));
+            u1 = df_add(u1, df_shfl_down(u1, o));
+        }
+        if (l == 0) decide((double)u0.hi + (double)u0.lo, (double)u1.hi + (double)u1.lo);
+    }
+    __syncthreads();
+    return true;
 }
 
 // shared-memory floats of a block owning `len` pixels of rows W wide
@@ -511,14 +512,11 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
                 pap += p[k] * ap[k];
             }
         }
-        double t0, t1;
-        ok = dn_allreduce(pap, 0.0f, s, red++, target, t0, t1);
-        if (!ok) break;
-        if (tid == 0) {
+        ok = dn_allreduce(pap, 0.0f, s, red++, target, [&](double t0, double) {
             if (!(t0 > 0.0)) s_done = 1;   // no direction left (solved, or breakdown)
-            else s_fa = (float)rz / (float)t0;   // used in FP32: the FP32 quotient
-        }
-        __syncthreads();
+            else s_fa = (float)rz / (float)t0;   // alpha, used in FP32
+        });
+        if (!ok) break;
         if (s_done) { done = 1; break; }
         const float fa = s_fa;
         // ---- x += alpha p, r -= alpha Ap, z = r / diag; r.z, r.r
@@ -539,16 +537,14 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
                 }
             }
         }
-        ok = dn_allreduce(rzp, rrp, s, red++, target, t0, t1);
-        if (!ok) break;
-        if (tid == 0) {
+        ok = dn_allreduce(rzp, rrp, s, red++, target, [&](double t0, double t1) {
             s_fb = rz > 0.0 ? (float)t0 / (float)rz : 0.0f;   // beta, used in FP32
             rz = t0;
             rr = t1;
             iters++;
             if (!(t0 > 0.0)) s_done = 1;   // r = 0: solved
-        }
-        __syncthreads();
+        });
+        if (!ok) break;
         if (s_done) { done = 1; break; }
         if ((it + 1) % kDnIters != 0 && it + 1 != s.max_iters) continue;
         // ---- residual replacement: r = b - A x in double, z = r / diag
@@ -592,14 +588,12 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
                 if (edge(o)) a.z[s0 + o] = z[k];
             }
         }
-        ok = dn_allreduce(rzp, rrp, s, red++, target, t0, t1);
-        if (!ok) break;
-        if (tid == 0) {
+        ok = dn_allreduce(rzp, rrp, s, red++, target, [&](double t0, double t1) {
             rz = t0;
             rr = t1;
             if (t1 <= a.tol2 * bb || !(t0 > 0.0)) s_done = 1;
-        }
-        __syncthreads();
+        });
+        if (!ok) break;
         done = s_done;
     }
 #pragma unroll
