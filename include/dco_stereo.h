@@ -377,9 +377,14 @@ dco_status dco_stereo_stream_status(dco_stereo *h, dco_stream stream);
  * vertical pass arms each tile's mbarrier but issues no copy, and waits only
  * a few polls, so every wait runs out with nothing in flight; the kernel
  * sets bit 0 of the status word and returns, and the stream status reads
- * DCO_ETIMEOUT.  0 restores normal operation.  Unknown bits: DCO_EINVAL.
+ * DCO_ETIMEOUT.  DCO_TEST_LOSE_GRID_ARRIVAL: in the one-launch
+ * densification solve, block 0 never arrives at the first grid barrier and
+ * every barrier waits only a few polls, so all blocks give up and return;
+ * dco_stereo_densify returns DCO_ETIMEOUT.  0 restores normal operation.
+ * Unknown bits: DCO_EINVAL.
  */
 #define DCO_TEST_LOSE_TILE_COPIES 1
+#define DCO_TEST_LOSE_GRID_ARRIVAL 4
 dco_status dco_stereo_set_test_flags(dco_stereo *h, int flags);
 
 /*

@@ -23,7 +23,8 @@ c_int, c_float, c_void_p, c_size_t = ctypes.c_int, ctypes.c_float, ctypes.c_void
 STATUS = {0: "DCO_OK", 1: "DCO_EINVAL", 2: "DCO_ENOMEM", 3: "DCO_EBUDGET", 4: "DCO_ECUDA",
           5: "DCO_ETIMEOUT", 6: "DCO_EDEVICE"}
 DCO_OK, DCO_EINVAL, DCO_ENOMEM, DCO_EBUDGET, DCO_ECUDA, DCO_ETIMEOUT, DCO_EDEVICE = range(7)
-DCO_TEST_LOSE_TILE_COPIES = 1   # failure test flag (include/dco_stereo.h)
+DCO_TEST_LOSE_TILE_COPIES = 1   # failure test flags (include/dco_stereo.h)
+DCO_TEST_LOSE_GRID_ARRIVAL = 4
 
 
 class Params(ctypes.Structure):

@@ -2677,7 +2677,7 @@ dco_status dco_stereo_stream_status(dco_stereo *h, dco_stream stream)
 
 dco_status dco_stereo_set_test_flags(dco_stereo *h, int flags)
 {
-    if (!h || (flags & ~DCO_TEST_LOSE_TILE_COPIES)) return DCO_EINVAL;
+    if (!h || (flags & ~(DCO_TEST_LOSE_TILE_COPIES | DCO_TEST_LOSE_GRID_ARRIVAL))) return DCO_EINVAL;
     h->test_flags = flags;
     return DCO_OK;
 }

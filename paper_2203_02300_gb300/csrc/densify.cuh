@@ -280,18 +280,22 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_resid(const DnArgs a)
 // the result does not depend on timing.  The residual replacement every
 // kDnIters iterations (in double-float arithmetic here, in double there) and
 // the convergence test on it follow the multi-launch path.  A grid barrier
-// that does not complete within kDnWaitLimit polls sets sc->lost and ends
-// the solve in every block.
+// that does not complete within s.wait_limit polls sets sc->lost and ends
+// the solve in every block (each later barrier also gives up after the
+// limit, so every block returns).
 constexpr int kDnSolveThreads = 1024;
 constexpr int kDnPx = 6;                  // pixels per thread
 constexpr int kDnIters = 16;              // iterations between residual replacements (even)
 constexpr int kDnWaitLimit = 1 << 22;     // polls of one grid barrier before the solve gives up
+constexpr int kDnTestWaitLimit = 64;      // the same, under the lost-arrival failure test
 constexpr int kDnHaloRound = 3;           // halo loads a thread issues together
 
 struct DnSolveArgs {
     DnArgs a;
     double *part;     // [2][nblocks][2] block partials, alternating between reductions
     int max_iters;
+    int wait_limit;   // polls of one grid barrier before the solve gives up
+    int skip_arrival; // failure test: block 0 never arrives at the first grid barrier
 };
 
 __device__ __forceinline__ unsigned dn_ld_acquire(const unsigned *p)
@@ -305,14 +309,15 @@ __device__ __forceinline__ unsigned dn_ld_acquire(const unsigned *p)
 // that starts at 0 for the solve (no reply awaited), and waits until it
 // reaches the block's running target (nblocks per barrier passed).  False
 // (in every thread) if the target was not seen within `limit` polls.
-__device__ __forceinline__ bool dn_grid_sync(unsigned *bar, unsigned &target, int limit)
+// arrive = false (the failure test) waits without arriving.
+__device__ __forceinline__ bool dn_grid_sync(unsigned *bar, unsigned &target, int limit, bool arrive)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
         __threadfence();
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(bar) : "memory");
+        if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(bar) : "memory");
         int ok = 0;
         for (int i = 0; i < limit; i++) {
             if ((int)(dn_ld_acquire(bar) - target) >= 0) { ok = 1; break; }
@@ -388,7 +393,8 @@ __device__ __forceinline__ bool dn_allreduce(float v0, float v1, const DnSolveAr
         }
         if (l == 0) part[blockIdx.x] = make_float4(u0.hi, u0.lo, u1.hi, u1.lo);
     }
-    if (!dn_grid_sync(&s.a.sc->bar, target, kDnWaitLimit)) return false;
+    const bool arrive = !(s.skip_arrival && blockIdx.x == 0 && red == 0);
+    if (!dn_grid_sync(&s.a.sc->bar, target, s.wait_limit, arrive)) return false;
     if (w == 0) {
         // lane l adds blocks l, l + 32, ...: the loads of a round of eight are
         // issued together (one L2 latency per 256 blocks)
@@ -710,12 +716,25 @@ dco_status dco_stereo_densify(dco_stereo *h, const float *d_sparse, const uint8_
         sa.a = a;
         sa.part = a.part;
         sa.max_iters = p.max_iters;
+        const bool lose = (h->test_flags & DCO_TEST_LOSE_GRID_ARRIVAL) != 0;
+        sa.wait_limit = lose ? kDnTestWaitLimit : kDnWaitLimit;
+        sa.skip_arrival = lose ? 1 : 0;
         void *args[] = {&sa};
+        cudaError_t e;
         {
             ProfScope ps(h, s, "k_dn_solve");
-            DCO_CUDA(h, cudaLaunchCooperativeKernel((const void *)k_dn_solve, dim3(sblk), dim3(kDnSolveThreads), args,
-                                                    ssmem, s));
+            e = cudaLaunchCooperativeKernel((const void *)k_dn_solve, dim3(sblk), dim3(kDnSolveThreads), args, ssmem, s);
         }
+        if (e == cudaErrorCooperativeLaunchTooLarge) {
+            // the device cannot hold the grid at once now (other work or a
+            // partitioned device): iterate with per-iteration launches instead
+            (void)cudaGetLastError();
+            one_launch = false;
+        } else {
+            DCO_CUDA(h, e);
+        }
+    }
+    if (one_launch) {
         h->launches += 1;
         DnScalars sc{};
         DCO_CUDA(h, cudaMemcpyAsync(&sc, a.sc, sizeof sc, cudaMemcpyDeviceToHost, s));

@@ -108,6 +108,30 @@ def test_lost_tile_copies_time_out_and_the_context_stays_usable(env):
     assert np.array_equal(got, want)
 
 
+def test_lost_grid_arrival_times_out_and_the_handle_stays_usable(env):
+    # failure test flag: in the one-launch densification solve, block 0 never
+    # arrives at the first grid barrier and every barrier waits only a few
+    # polls, so all blocks give up and return (no trap, no hang); the call
+    # reports DCO_ETIMEOUT and the same handle then solves normally
+    torch, binding, _ = env
+    rng = np.random.default_rng(12)
+    H, W = 64, 96
+    ds = np.where(rng.random((H, W)) < 0.2, rng.uniform(0.5, 5.0, (H, W)), 0.0).astype(np.float32)
+    mi = rng.random((H, W)).astype(np.float32)
+    d_ds, d_mi = _dev(torch, ds), _dev(torch, mi)
+    p = binding.DenseParams.default(tol=1e-6)
+    with binding.Stereo(0) as h:
+        want = h.densify(d_ds, None, d_mi, d_mi, None, p).cpu().numpy()
+        h.set_test_flags(binding.DCO_TEST_LOSE_GRID_ARRIVAL)
+        with pytest.raises(binding.DcoError) as e:
+            h.densify(d_ds, None, d_mi, d_mi, None, p)
+        assert e.value.code == binding.DCO_ETIMEOUT
+        h.set_test_flags(0)
+        got = h.densify(d_ds, None, d_mi, d_mi, None, p).cpu().numpy()
+        torch.cuda.synchronize()
+    assert np.array_equal(got, want)
+
+
 def test_stream_status_waits_for_its_own_stream(env):
     torch, binding, _ = env
     s = scenes.config_scene(1)
