@@ -400,7 +400,7 @@ dco_status dco_stereo_set_test_flags(dco_stereo *h, int flags);
  *     before any stream capture.
  *   - Sizes whose workspace (passes of 32 disparities) does not fit the
  *     array return DCO_EBUDGET before anything is enqueued: roughly
- *     W*H <= 90 000 pixels (e.g. 320x240) at any D <= 256.
+ *     W*H <= 80 000 pixels (e.g. 320x240) at any D <= 256.
  *   - All calls share the one array and it keeps the last call's contents;
  *     nothing in it needs to start at zero (every word a kernel reads was
  *     written earlier in the same call; the tables are written by a kernel

@@ -420,8 +420,12 @@ __device__ __forceinline__ void prep_body(const PrepArgs &a, int bx, int by, int
     }
     const int lmin = min(min(arm[0], arm[1]), min(arm[2], arm[3]));
     const float alphaS = __ldg(a.tables + kTabAD + kTabCen + lmin);
+    const uint32_t colour = unspread10(p) | (uint32_t(lmin) << 24);
     (img ? a.rec[1] : a.rec[0])[(size_t)y * a.rpitch + x] =
-        make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), unspread10(p) | (uint32_t(lmin) << 24), __float_as_uint(alphaS));
+        make_uint4((uint32_t)bits, (uint32_t)(bits >> 32), colour, __float_as_uint(alphaS));
+    const size_t pe = (size_t)y * 2 * a.phw + (size_t)(x & 1) * a.phw + (x >> 1);
+    (img ? a.cen[1] : a.cen[0])[pe] = make_uint2((uint32_t)bits, (uint32_t)(bits >> 32));
+    (img ? a.col[1] : a.col[0])[pe] = colour;
     (img ? a.arms[1] : a.arms[0])[i] = make_uchar4((uint8_t)arm[0], (uint8_t)arm[1], (uint8_t)arm[2], (uint8_t)arm[3]);
 }
 
@@ -492,19 +496,65 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a copy is declared lost
+constexpr int kTestWaitLimit = 64;    // the same, under the lost-copy failure test
+constexpr int kStatusCopyTimeout = 1; // status word: a copy (k_hagg staging, k_vagg tiles) did not complete
+constexpr int kStatusAlign = 2;       // status word: shared memory not aligned for the tile copies
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// bounded wait for the phase of the given parity to complete: false after
+// `limit` polls without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; i++) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// bulk copy of n bytes (a multiple of 16; both addresses 16-byte aligned)
+// from global memory to shared memory, completing on mbarrier `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t n, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(n), "r"(bar)
+                 : "memory");
+}
+
 // byte offsets of the H block's shared-memory regions.  Candidate indices
 // run over [0, len + 31); index i sits at position i >> 1 of the even (i & 1
-// = 0) or odd array, hh positions each.
+// = 0) or odd array, hh positions each.  The arrays arrive by bulk copies
+// that start on 16-byte boundaries of the candidate planes, so each half has
+// room for the alignment shift: census halves hhc entries (up to one more
+// than hh, even), colour halves hhk (up to three more, a multiple of 4), the
+// arms up to three entries more.
 struct HSmem {
-    int ref, oth, hh, col, arm, p, t, total;
+    int ref, oth, hh, hhc, hhk, col, arm, p, t, total;
     __host__ __device__ HSmem(int len, int chunk, int nw)
     {
         ref = kTabBytes;
-        oth = ref + len * 16;                   // census: uint2 [2][hh]; then the segment offsets
+        oth = ref + len * 16;                   // census: uint2 [2][hhc]; then the segment offsets
         hh = (len + 33) / 2;
-        col = oth + hh * 16;                    // colour: uint32 [2][hh]
-        arm = oth + (hh * 24 + 15) / 16 * 16;
-        p = arm + (chunk + 3) / 4 * 16 + 128;   // one zero row in front: P[-1]
+        hhc = (hh + 3) & ~1;
+        hhk = (hh + 9) & ~3;
+        col = oth + hhc * 16;                   // colour: uint32 [2][hhk]
+        arm = col + hhk * 8;
+        p = arm + ((chunk + 9) & ~3) * 4 + 128; // one zero row in front: P[-1]
         t = p + len * 128;
         total = t + 2 * nw * 128;               // segment totals [2 nw][32]
     }
@@ -581,17 +631,17 @@ __device__ __forceinline__ void hagg_tail(const uint32_t *P, uint32_t *T, const 
 // and the previous one with da + 1, view 1 the other way round.  A match
 // outside the image costs 1 (Sint): view 0 needs x >= va / vb, view 1 x < va / vb.
 template <int kView>
-__device__ __forceinline__ void hagg_costs(const uint4 *sref, const uint2 *scen, const uint32_t *scol, int hh,
-                                           const float *sTA, const float *sTC, uint32_t *P, int sa, int sb, int hl,
-                                           int va, int vb, float Sf, uint32_t Sint, uint32_t &run_a,
-                                           uint32_t &run_b)
+__device__ __forceinline__ void hagg_costs(const uint4 *sref, const uint2 *cenE, const uint2 *cenO,
+                                           const uint32_t *colE, const uint32_t *colO, const float *sTA,
+                                           const float *sTC, uint32_t *P, int sa, int sb, int hl, int va, int vb,
+                                           float Sf, uint32_t Sint, uint32_t &run_a, uint32_t &run_b)
 {
     const int nb = kView ? 1 + 2 * hl : 31 - 2 * hl;
     const int p0 = (sa + nb - 1) >> 1;
-    const uint2 *cE = scen + p0 + 1, *cO = scen + hh + p0;   // new records at odd / even steps
-    const uint32_t *kE = scol + p0 + 1, *kO = scol + hh + p0;
-    uint2 pc = scen[p0];
-    uint32_t pk = scol[p0];
+    const uint2 *cE = cenE + p0 + 1, *cO = cenO + p0;   // new records at odd / even steps
+    const uint32_t *kE = colE + p0 + 1, *kO = colO + p0;
+    uint2 pc = cenE[p0];
+    uint32_t pk = colE[p0];
     uint2 *Pp = reinterpret_cast<uint2 *>(P) + hl;
     auto cost = [&](const uint4 &pr, float av, float sav, uint2 c, uint32_t col) -> uint32_t {
         const int h = __popc(pr.x ^ c.x) + __popc(pr.y ^ c.y);
@@ -636,43 +686,86 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     float *sTA = reinterpret_cast<float *>(smem_raw);
     float *sTC = sTA + kTabAD;
     uint4 *sref = reinterpret_cast<uint4 *>(smem_raw + L.ref);
-    uint2 *scen = reinterpret_cast<uint2 *>(smem_raw + L.oth);       // candidate census [2][hh]
-    uint32_t *scol = reinterpret_cast<uint32_t *>(smem_raw + L.col); // candidate colour + Lmin [2][hh]
+    uint2 *scen = reinterpret_cast<uint2 *>(smem_raw + L.oth);       // candidate census [2][hhc]
+    uint32_t *scol = reinterpret_cast<uint32_t *>(smem_raw + L.col); // candidate colour + Lmin [2][hhk]
     uchar4 *sarm = reinterpret_cast<uchar4 *>(smem_raw + L.arm);
     uint32_t *P = reinterpret_cast<uint32_t *>(smem_raw + L.p);   // [len][32], P[-1] = 0
     uint32_t *T = reinterpret_cast<uint32_t *>(smem_raw + L.t);   // [2 nw][32]
     if (threadIdx.x < 32) P[(int)threadIdx.x - 32] = 0u;
 
-    // disparities of this group: [dlo, dhi] live
+    // first disparity of this group
     const int dlo = a.d0 + 32 * g;
-    const int dhi = min(min(a.d0 + a.dc, a.D), dlo + 32) - 1;
     // candidate index i <-> column olo + i, i in [0, len + 31): every
-    // disparity of the 32-wide group; the indices of live disparities are
-    // [ilo, ihi), the others are zero-filled (their outputs are never read)
+    // disparity of the 32-wide group (the costs of dead disparities are
+    // computed from whatever the padded planes hold and never read)
     const int olo = view ? xa + dlo : xa - dlo - 31;
-    const int olen = len + 31;
-    const int ilo = view ? 0 : 31 - (dhi - dlo), ihi = view ? len + dhi - dlo : olen;
     const uint4 *rref = (view ? a.rec[1] : a.rec[0]) + (size_t)y * a.rpitch;
-    const uint4 *roth = (view ? a.rec[0] : a.rec[1]) + (size_t)y * a.rpitch;   // padded: live olo + i >= -255
-    const uchar4 *aref = (view ? a.arms[1] : a.arms[0]) + (size_t)y * W;
 
-    // ---- 0: stage
-    for (int i = threadIdx.x; i < kTabBytes / 16; i += blockDim.x)
-        cp_async16(smem_raw + 16 * i, reinterpret_cast<const uint8_t *>(a.tables) + 16 * i);
-    for (int i = threadIdx.x; i < len; i += blockDim.x) cp_async16(sref + i, rref + xa + i);
-    for (int i = threadIdx.x; i < olen; i += blockDim.x) {
-        const int pos = (i & 1) * L.hh + (i >> 1);
-        if (i >= ilo && i < ihi) {
-            cp_async8(scen + pos, &roth[olo + i].x);   // census words
-            cp_async4(scol + pos, &roth[olo + i].z);   // colour and Lmin
-        } else {
-            scen[pos] = make_uint2(0u, 0u);
-            scol[pos] = 0u;
+    // ---- 0: stage by bulk copies, issued by one thread on one mbarrier:
+    // the tables, the reference records, the arms and the candidates.  The
+    // even-index candidates i = 2m are the columns olo + 2m, entry
+    // (olo >> 1) + m of one half of the other view's plane row, the odd ones
+    // olo + 1 + 2m of the other half; only the in-image columns are copied
+    // (the others cost 1 whatever they hold).  Each copy starts on the 16-byte
+    // boundary at or below its first entry, and candidate m of a half sits at
+    // shared position o + m, o (0-3) chosen so the copy's destination is
+    // 16-byte aligned too.
+    __shared__ __align__(8) unsigned long long hbar_s;
+    __shared__ int hoff_s[5];   // the halves' shared offsets o, then the lost flag
+    const uint32_t hbar = (uint32_t)__cvta_generic_to_shared(&hbar_s);
+    const size_t ga = (size_t)y * W + xs, gas = ga & ~(size_t)3;
+    if (threadIdx.x == 0) {
+        struct Half {
+            int base, mlo, mhi;   // plane entry of m = 0 (may be negative), in-image m range
+        };
+        auto cand_half = [&](int c0) {   // the candidates c0 + 2m, m < hh
+            Half h;
+            h.base = (c0 & 1) * a.phw + (c0 >> 1);
+            h.mlo = max(0, (1 - c0) >> 1);          // first m with c0 + 2m >= 0
+            h.mhi = min(L.hh, (W - c0 + 1) >> 1);   // first m with c0 + 2m >= W
+            return h;
+        };
+        const Half hE = cand_half(olo), hO = cand_half(olo + 1);
+        // q entries per 16 bytes: the copy starts `shift` entries below the
+        // first in-image one; o makes (o + mlo - shift) a multiple of q
+        auto shift = [](const Half &h, int q) { return h.mlo < h.mhi ? (h.base + h.mlo) & (q - 1) : 0; };
+        auto offs = [&](const Half &h, int q) { return (shift(h, q) - h.mlo) & (q - 1); };
+        auto count = [&](const Half &h, int q) {
+            return h.mlo < h.mhi ? (uint32_t)(h.mhi - h.mlo + shift(h, q) + q - 1) & ~(uint32_t)(q - 1) : 0u;
+        };
+        const uint2 *cpl = (view ? a.cen[0] : a.cen[1]) + (size_t)y * 2 * a.phw;
+        const uint32_t *kpl = (view ? a.col[0] : a.col[1]) + (size_t)y * 2 * a.phw;
+        const uint32_t nA = (uint32_t)(xe - xs + (int)(ga - gas) + 3) & ~3u;
+        const uint32_t nCE = count(hE, 2), nCO = count(hO, 2), nKE = count(hE, 4), nKO = count(hO, 4);
+        const int oCE = offs(hE, 2), oCO = offs(hO, 2), oKE = offs(hE, 4), oKO = offs(hO, 4);
+        mbar_init(hbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        mbar_expect_tx(hbar, (uint32_t)kTabBytes + 16u * (uint32_t)len + 8u * (nCE + nCO) + 4u * (nKE + nKO) + 4u * nA);
+        bulk_g2s(smem_raw, a.tables, kTabBytes, hbar);
+        bulk_g2s(sref, rref + xa, 16u * (uint32_t)len, hbar);
+        bulk_g2s(sarm, (view ? a.arms[1] : a.arms[0]) + gas, 4u * nA, hbar);
+        if (nCE) bulk_g2s(scen + oCE + hE.mlo - shift(hE, 2), cpl + hE.base + hE.mlo - shift(hE, 2), 8u * nCE, hbar);
+        if (nCO)
+            bulk_g2s(scen + L.hhc + oCO + hO.mlo - shift(hO, 2), cpl + hO.base + hO.mlo - shift(hO, 2), 8u * nCO, hbar);
+        if (nKE) bulk_g2s(scol + oKE + hE.mlo - shift(hE, 4), kpl + hE.base + hE.mlo - shift(hE, 4), 4u * nKE, hbar);
+        if (nKO)
+            bulk_g2s(scol + L.hhk + oKO + hO.mlo - shift(hO, 4), kpl + hO.base + hO.mlo - shift(hO, 4), 4u * nKO, hbar);
+        hoff_s[0] = oCE;
+        hoff_s[1] = oCO;
+        hoff_s[2] = oKE;
+        hoff_s[3] = oKO;
+        const bool ok = mbar_wait(hbar, 0u, a.wait_limit);
+        if (!ok) {   // report, and wait (bounded) once more before the block's shared memory is released
+            if (a.status) atomicOr(a.status, kStatusCopyTimeout);
+            mbar_wait(hbar, 0u, a.wait_limit);
         }
+        hoff_s[4] = !ok;
     }
-    for (int i = threadIdx.x; i < xe - xs; i += blockDim.x) cp_async4(sarm + i, aref + xs + i);
-    cp_async_wait_all();
     __syncthreads();
+    if (hoff_s[4]) return;
+    const uint2 *cenE = scen + hoff_s[0], *cenO = scen + L.hhc + hoff_s[1];
+    const uint32_t *colE = scol + hoff_s[2], *colO = scol + L.hhk + hoff_s[3];
+    const uchar4 *sarm0 = sarm + (ga - gas);   // arm of output column xs
 
     // ---- A: costs and local prefixes of this half-warp's segment
     const int half = lane >> 4, hl = lane & 15;
@@ -684,9 +777,9 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     uint32_t run_a = 0, run_b = 0;
     if (sa < len) {
         if (view)
-            hagg_costs<1>(sref, scen, scol, L.hh, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
+            hagg_costs<1>(sref, cenE, cenO, colE, colO, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
         else
-            hagg_costs<0>(sref, scen, scol, L.hh, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
+            hagg_costs<0>(sref, cenE, cenO, colE, colO, sTA, sTC, P, sa, sb, hl, va, vb, a.S, a.Sint, run_a, run_b);
     }
     reinterpret_cast<uint2 *>(T + s * 32)[hl] = make_uint2(run_a, run_b);
     __syncthreads();
@@ -704,7 +797,7 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     __syncthreads();
 
     // ---- C
-    hagg_out_quads<4>(P, OFF, sarm, xe - xs, xs - xa,
+    hagg_out_quads<4>(P, OFF, sarm0, xe - xs, xs - xa,
                       (view ? a.sh[1] : a.sh[0]) + ((size_t)y * W + xs) * a.dstride + g * 32, a.dstride);
 }
 
@@ -935,10 +1028,6 @@ __device__ __forceinline__ void hvote_body(const HVArgs &a, int bx, int by, int 
 constexpr int kQS = 36;   // Q row stride in words
 constexpr int kVSeg = 32; // rows per warp
 constexpr int kQ0 = 64;   // Q[0] at word 64 (256 bytes): every warp's tile starts on a 128-byte boundary
-constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a copy is declared lost
-constexpr int kTestWaitLimit = 64;    // the same, under the lost-copy failure test
-constexpr int kStatusCopyTimeout = 1; // status word: a tile copy did not complete
-constexpr int kStatusAlign = 2;       // status word: shared memory not aligned for the tile copies
 constexpr uint32_t kVTileBytes = kVSeg * kQS * 4;
 
 // words before the mbarriers: Q[-1] (zeros, at kQ0 - kQS) and Q [nw*32 rows:
@@ -949,31 +1038,6 @@ __host__ __device__ inline size_t vagg_bar_word(int len, int nw)
 }
 __host__ __device__ inline size_t vagg_smem_words(int len, int nw) { return vagg_bar_word(len, nw) + 2 * nw; }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-// bounded wait for the phase of the given parity to complete: false after
-// `limit` polls without completion
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
-{
-    for (int i = 0; i < limit; i++) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, uint32_t bar)
 {
     asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -1385,8 +1449,8 @@ struct Derived {
 };
 
 struct Layout {
-    size_t rgbx[2], grey[2], rec[2], arms[2], atmp[2], best[2], disp[2], sh[2], vtmp, total;
-    int dc, dstride, npass, rpitch;
+    size_t rgbx[2], grey[2], rec[2], cen[2], col[2], arms[2], atmp[2], best[2], disp[2], sh[2], vtmp, total;
+    int dc, dstride, npass, rpitch, phw;
 };
 
 constexpr size_t kAlign = 256;
@@ -1455,10 +1519,15 @@ Layout make_layout(int W, int H, int D, const dco_params &p, int dc_override = 0
     L.npass = (D + dc - 1) / dc;
     size_t off = 0;
     L.rpitch = W + 2 * kRPad;
+    L.phw = ((W + 1) / 2 + 3) / 4 * 4;
     for (int v = 0; v < 2; v++) { L.rgbx[v] = off; off = align_up(off + 4 * npx); }
     for (int v = 0; v < 2; v++) { L.grey[v] = off; off = align_up(off + npx); }
     for (int v = 0; v < 2; v++) { L.rec[v] = off; off = align_up(off + 16 * (size_t)H * L.rpitch); }
-    for (int v = 0; v < 2; v++) { L.arms[v] = off; off = align_up(off + 4 * npx); }
+    // candidate planes, 16 bytes of slack each (the bulk copies end on 16-byte boundaries)
+    for (int v = 0; v < 2; v++) { L.cen[v] = off; off = align_up(off + 8 * (size_t)H * 2 * L.phw + 16); }
+    for (int v = 0; v < 2; v++) { L.col[v] = off; off = align_up(off + 4 * (size_t)H * 2 * L.phw + 16); }
+    // arms: 16 bytes of slack, read by the cost pass's bulk copies past the last pixel
+    for (int v = 0; v < 2; v++) { L.arms[v] = off; off = align_up(off + 4 * npx + 16); }
     for (int v = 0; v < 2; v++) { L.atmp[v] = off; off = align_up(off + (p.smooth_arms ? 4 * npx : 0)); }
     for (int v = 0; v < 2; v++) { L.best[v] = off; off = align_up(off + (L.npass > 1 ? 8 * npx : 0)); }
     for (int v = 0; v < 2; v++) { L.disp[v] = off; off = align_up(off + 2 * npx); }
@@ -1918,8 +1987,11 @@ dco_status launch_prep(dco_stereo *h, const dco_params &p, const Derived &dv, co
             b.a.rgbx[v] = jptr<uint32_t>(h, j, j.L.rgbx[v]);
             b.a.grey[v] = jptr<uint8_t>(h, j, j.L.grey[v]);
             b.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
+            b.a.cen[v] = jptr<uint2>(h, j, j.L.cen[v]);
+            b.a.col[v] = jptr<uint32_t>(h, j, j.L.col[v]);
             b.a.arms[v] = jptr<uchar4>(h, j, j.L.arms[v]);
         }
+        b.a.phw = j.L.phw;
         if (j.arms0) b.a.arms[0] = j.arms0;
         b.a.tables = h->d_tables;
         b.a.W = j.W; b.a.H = j.H; b.a.rpitch = j.L.rpitch;
@@ -2043,9 +2115,14 @@ dco_status launch_pass(dco_stereo *h, const Derived &dv, const std::vector<Job> 
         Item<HArgs> a{};
         for (int v = 0; v < 2; v++) {
             a.a.rec[v] = jptr<uint4>(h, j, j.L.rec[v]) + kRPad;
+            a.a.cen[v] = jptr<uint2>(h, j, j.L.cen[v]);
+            a.a.col[v] = jptr<uint32_t>(h, j, j.L.col[v]);
             a.a.arms[v] = jptr<uchar4>(h, j, j.L.arms[v]);
             a.a.sh[v] = jptr<uint32_t>(h, j, j.L.sh[v]);
         }
+        a.a.phw = j.L.phw;
+        a.a.status = h->d_status;
+        a.a.wait_limit = kWaitLimit;
         a.a.tables = h->d_tables;
         a.a.W = j.W; a.a.H = j.H; a.a.D = dv.dmin + j.D; a.a.rpitch = j.L.rpitch;
         a.a.d0 = d0; a.a.dc = dc; a.a.dstride = j.L.dstride;

@@ -35,6 +35,12 @@ constexpr int kTabFloats = kTabAD + kTabCen + kTabAlpha;
 // discarded: the cost of a match outside the image is 1).
 constexpr int kRPad = 256;
 
+// Candidate planes (read by the cost pass's bulk copies): per image and
+// row, the census words (uint2) and the colours (uint32) of the even
+// columns, then of the odd columns, each half phw entries long (ceil(W / 2)
+// rounded up to a multiple of 4, so every half starts on a 16-byte
+// boundary); 16 bytes of slack after the last row.
+
 // The cost H pass gives each warp kHSegCost columns of the prefix range (two
 // half-warp segments of 16; one chunk per row up to kHMaxLen columns, else
 // 512-column chunks), k_vcost each warp kHSegCost rows, the vote H pass
@@ -57,6 +63,9 @@ struct PrepArgs {
     const uint32_t *rgbx[2];
     const uint8_t *grey[2];
     uint4 *rec[2];         // first real record of row 0; row pitch rpitch
+    uint2 *cen[2];         // candidate planes (census, colour): row y, column x at
+    uint32_t *col[2];      //   y * 2 phw + (x & 1) * phw + (x >> 1)
+    int phw;
     uchar4 *arms[2];
     const float *tables;   // alpha*S table at offset kTabAD + kTabCen
     int W, H, rpitch;
@@ -66,6 +75,11 @@ struct PrepArgs {
 
 struct HArgs {
     const uint4 *rec[2];   // padded rows, pitch rpitch
+    const uint2 *cen[2];   // candidate planes (PrepArgs)
+    const uint32_t *col[2];
+    int phw;
+    int *status;           // device status word (a lost staging copy sets bit 0)
+    int wait_limit;        // mbarrier polls before the staging copies are declared lost
     const uchar4 *arms[2];
     uint32_t *sh[2];
     const float *tables;
