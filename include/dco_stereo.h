@@ -43,9 +43,10 @@
  *     read with dco_stereo_sync_status() or dco_stereo_stream_status().  The
  *     vertical pass sets bit 0 when a TMA tile copy does not complete within
  *     its bounded mbarrier wait (reported as DCO_ETIMEOUT; the block stops
- *     issuing copies and returns) and bit 1 when its shared memory is not
- *     128-byte aligned for the copies (DCO_EDEVICE); the pass's outputs are
- *     then not valid.
+ *     issuing copies and returns), and so does the cost pass when its
+ *     staging bulk copies do not; bit 1 when the vertical pass's shared
+ *     memory is not 128-byte aligned for the copies (DCO_EDEVICE); the
+ *     pass's outputs are then not valid.
  */
 #ifndef DCO_STEREO_H
 #define DCO_STEREO_H
@@ -358,8 +359,8 @@ size_t dco_stereo_workspace_allocated(dco_stereo *h);
 
 /*
  * Waits for all work of the handle's device, then reads and clears the
- * device status word.  DCO_OK; DCO_ETIMEOUT if a tile copy of the vertical
- * pass did not complete within its bounded wait; DCO_EDEVICE if a kernel
+ * device status word.  DCO_OK; DCO_ETIMEOUT if a copy of the cost or the
+ * vertical pass did not complete within its bounded wait; DCO_EDEVICE if a kernel
  * reported another failed internal check since the last read.
  */
 dco_status dco_stereo_sync_status(dco_stereo *h);
