@@ -375,10 +375,10 @@ dco_status dco_stereo_stream_status(dco_stereo *h, dco_stream stream);
 
 /*
  * Failure tests (not for normal use).  DCO_TEST_LOSE_TILE_COPIES: the
- * vertical pass arms each tile's mbarrier but issues no copy, and waits only
- * a few polls, so every wait runs out with nothing in flight; the kernel
- * sets bit 0 of the status word and returns, and the stream status reads
- * DCO_ETIMEOUT.  DCO_TEST_LOSE_GRID_ARRIVAL: in the one-launch
+ * cost pass's staging and the vertical pass's tiles arm their mbarriers but
+ * issue no copy, and wait only a few polls, so every wait runs out with
+ * nothing in flight; the kernels set bit 0 of the status word and return,
+ * and the stream status reads DCO_ETIMEOUT.  DCO_TEST_LOSE_GRID_ARRIVAL: in the one-launch
  * densification solve, block 0 never arrives at the first grid barrier and
  * every barrier waits only a few polls, so all blocks give up and return;
  * dco_stereo_densify returns DCO_ETIMEOUT.  0 restores normal operation.

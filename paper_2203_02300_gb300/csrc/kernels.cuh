@@ -80,6 +80,7 @@ struct HArgs {
     int phw;
     int *status;           // device status word (a lost staging copy sets bit 0)
     int wait_limit;        // mbarrier polls before the staging copies are declared lost
+    int skip_copy;         // failure test: arm the staging barrier but issue no copy
     const uchar4 *arms[2];
     uint32_t *sh[2];
     const float *tables;
