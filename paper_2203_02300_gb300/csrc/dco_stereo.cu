@@ -697,7 +697,7 @@ __device__ __forceinline__ void hagg_body(const HArgs &a, int bx, int by, int bz
     const int dlo = a.d0 + 32 * g;
     // candidate index i <-> column olo + i, i in [0, len + 31): every
     // disparity of the 32-wide group (the costs of dead disparities are
-    // computed from whatever the padded planes hold and never read)
+    // computed from whatever the shared words hold and never read)
     const int olo = view ? xa + dlo : xa - dlo - 31;
     const uint4 *rref = (view ? a.rec[1] : a.rec[0]) + (size_t)y * a.rpitch;
 
