@@ -269,10 +269,10 @@ __global__ void __launch_bounds__(kDnBlock) k_dn_resid(const DnArgs a)
 // The whole CG loop in one cooperative launch.  Block b owns the pixels
 // [s_b, e_b) of the row-major image (an equal share); thread t the pixels
 // s_b + t + k * blockDim.x, k < kDnPx, whose x, r, z, p and Ap stay in
-// registers for the whole solve.  Shared memory holds the diagonal, the
-// block's weights over [s_b - W, e_b), p over [s_b - W, e_b + W) for the
-// stencil, and p of the two halo bands (the W pixels before and after the
-// share), which every
+// registers for the whole solve.  Shared memory holds the diagonal and its
+// reciprocal (the Jacobi preconditioner as a multiply), the block's weights
+// over [s_b - W, e_b), p over [s_b - W, e_b + W) for the stencil, and p of
+// the two halo bands (the W pixels before and after the share), which every
 // block forms itself from the owners' z (exchanged through global memory)
 // and the common beta, so an iteration needs two grid barriers: one per dot
 // product.  Every block adds the blocks' partial sums in the same fixed
@@ -423,7 +423,7 @@ __device__ __forceinline__ bool dn_allreduce(float v0, float v1, const DnSolveAr
 }
 
 // shared-memory floats of a block owning `len` pixels of rows W wide
-__host__ __device__ inline size_t dn_solve_smem_floats(long len, int W) { return 4 * (size_t)len + 6 * (size_t)W; }
+__host__ __device__ inline size_t dn_solve_smem_floats(long len, int W) { return 5 * (size_t)len + 6 * (size_t)W; }
 
 __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_constant__ DnSolveArgs s)
 {
@@ -435,8 +435,10 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
     const int len = (int)(e0 - s0);
     // PS: p (x in the residual replacement) over [s0 - W, e0 + W), index i - s0 + W;
     // WR, WD: weights over [s0 - W, e0), same index; PH: p of the halo bands;
-    // DG: the diagonal of the share, index i - s0
+    // DG: the diagonal of the share, index i - s0; RD: its reciprocal (0 where
+    // the diagonal is 0), so the preconditioner z = r / diag is one multiply
     float *PS = dsm, *WR = PS + len + 2 * W, *WD = WR + len + W, *PH = WD + len + W, *DG = PH + 2 * W;
+    float *RD = DG + len;
     const float ls2 = 2.0f * a.lambda_s;
     auto halo_pixel = [&](int k) -> long { return k < W ? s0 - W + k : e0 + (k - W); };   // k < 2 W
     auto halo_slot = [&](int k) -> int { return k < W ? k : len + W + (k - W); };         // its PS index
@@ -446,7 +448,11 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
         WD[k] = i >= 0 ? a.wd[i] : 0.0f;
     }
     for (int k = tid; k < 2 * W; k += nt) PH[k] = 0.0f;
-    for (int k = tid; k < len; k += nt) DG[k] = a.dg[s0 + k];
+    for (int k = tid; k < len; k += nt) {
+        const float d = a.dg[s0 + k];
+        DG[k] = d;
+        RD[k] = d > 0.0f ? 1.0f / d : 0.0f;
+    }
     float x[kDnPx], r[kDnPx], z[kDnPx], p[kDnPx], ap[kDnPx];
 #pragma unroll
     for (int k = 0; k < kDnPx; k++) {
@@ -533,8 +539,7 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
             if (o < len) {
                 x[k] += fa * p[k];
                 r[k] -= fa * ap[k];
-                const float d = DG[o];
-                z[k] = d > 0.0f ? r[k] / d : 0.0f;
+                z[k] = r[k] * RD[o];
                 rzp += r[k] * z[k];
                 rrp += r[k] * r[k];
                 if (edge(o)) {
@@ -588,7 +593,7 @@ __global__ void __launch_bounds__(kDnSolveThreads, 1) k_dn_solve(const __grid_co
                 df rd = df_add(df_scale(nb, ls2), df_prod(-d, x[k]));
                 rd = df_add(rd, df{a.b[s0 + o], 0.0f});
                 r[k] = __fadd_rn(rd.hi, rd.lo);
-                z[k] = d > 0.0f ? r[k] / d : 0.0f;
+                z[k] = r[k] * RD[o];
                 rzp += r[k] * z[k];
                 rrp += r[k] * r[k];
                 if (edge(o)) a.z[s0 + o] = z[k];
